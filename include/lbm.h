@@ -1,0 +1,195 @@
+/*
+ * lbm.h — C ABI of the B300 library for the fluid–filament method of
+ * "Evaporation-Driven Nanowire Self-Assembly in an Elongated Droplet"
+ * (Schoettner, Xie, Harting), Sec. II.
+ *
+ * One handle holds one or more lattice instances (a batch) that advance
+ * together on one CUDA stream.  Each time step of each instance is
+ *   stream (Eq. (1), left side)  ->  moments (Eq. (3))
+ *   -> wetting ghost layer + colour gradient + curvature + CSF force (Sec. II.A)
+ *   -> filament sub-steps with two-way drag coupling (Eqs. (9)-(12))
+ *   -> colour-blind forced BGK (Eqs. (1)-(2)) -> recolouring
+ *   -> evaporation sink (Eq. (8))
+ * computed by hand-written sm_103a kernels.  There is no CPU fallback.
+ *
+ * Conventions
+ *  - The caller owns all device memory: it allocates one workspace of
+ *    lbm_workspace_bytes() bytes (16-byte aligned) and passes it to
+ *    lbm_create().  The library never allocates device memory.
+ *  - Host arrays passed to a call are borrowed for that call only.
+ *  - Every call returns a status.  Kernel-side failures (NaN density, FENE
+ *    overstretch, bead out of range, capacity overflow) are latched in a
+ *    device flag word; lbm_sync() and every call that reads data back
+ *    report them.  Once latched, a failure stays until lbm_clear_error().
+ *  - lbm_step() only enqueues work on the handle's stream and returns.
+ *  - Lattice arrays are x-fastest: index = (z*ny + y)*nx + x.
+ *  - Units are lattice units; rho0 = 1 is the reference density.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,      /* invalid argument or configuration */
+    LBM_ENOMEM_WS = 2,   /* workspace smaller than lbm_workspace_bytes() */
+    LBM_ECUDA = 3,       /* a CUDA runtime call failed */
+    LBM_ENAN = 4,        /* non-finite or non-positive density met in a step */
+    LBM_EFENE = 5,       /* a FENE bond reached R_m (Eq. (9) undefined there) */
+    LBM_EBEAD_OOB = 6,   /* a bead left the fluid or moved > 0.5 in one step */
+    LBM_ETIMEOUT = 7,    /* a bounded device-side wait gave up */
+    LBM_ESTATE = 8,      /* call not valid in the handle's current state */
+    LBM_ECAPACITY = 9    /* bead, neighbour or contact capacity exceeded */
+} lbm_status;
+
+/* Storage precision of the populations.  FP64 and FP32 store f^R and f^B.
+ * The two shifted forms store, per direction, the total population as its
+ * deviation from rest, F_i - w_i rho0, and the liquid fraction f^R_i/F_i - 1/2,
+ * both as 16-bit numbers; collision, forcing and moments run in FP32, mass
+ * and evaporation sums and the bead integration stay FP64. */
+typedef enum {
+    LBM_FP64 = 0,
+    LBM_FP32 = 1,
+    LBM_FP16_SHIFTED = 2,
+    LBM_BF16_SHIFTED = 3
+} lbm_precision;
+
+typedef struct lbm_config {
+    int nx, ny, nz;        /* lattice size; x, y periodic; wall below z = 0 */
+    int prec;              /* lbm_precision (must be equal across a batch) */
+    double tau_R, tau_B;   /* relaxation times of liquid (R) and gas (B), Eq. (1) */
+    double beta;           /* recolouring strength (Sec. II.A, colour-gradient method) */
+    double sigma;          /* surface tension of the CSF force F = sigma/2 kappa grad C */
+    double rho0;           /* reference density, Eq. (3) */
+    double J0;             /* evaporation rate scale, Eq. (8); 0 disables evaporation */
+    double K;              /* kinetic resistance, Eq. (8) (paper: 0.01) */
+    long long evap_start;  /* first step with the sink on; < 0 never */
+    int top_bc;            /* 0: bounce-back wall at the top; 1: pure-gas equilibrium inflow */
+    double body[3];        /* uniform body-force density (0 for the paper's runs) */
+    /* initial droplet (Sec. III): C = tanh(-(q-1) min(a,b,c)/width) */
+    int shape;             /* 0 ellipsoid (cap if cz < 0), 1 elliptic cylinder along x */
+    double cx, cy, cz;     /* centre */
+    double a, b, c;        /* semi-axes (for shape 1, a is the half-length) */
+    double width;          /* interface width of the tanh profile */
+    double theta_deg;      /* uniform contact angle until lbm_set_substrate_pattern() */
+    /* filaments, Eqs. (9)-(12) and the filament paragraph of Sec. II.A */
+    double ks, Rm;         /* FENE (paper: 0.3, 2.4) */
+    double d0, eps_wca;    /* bead diameter and WCA strength (paper: 2, 0.03) */
+    double kb;             /* bending constant (paper: 8) */
+    double eps_coh;        /* cohesive LJ well depth between filaments (eps* x eps_s) */
+    double eps_s;          /* substrate adhesion (paper: 0.006) */
+    double rc;             /* cut-off of the cohesive and substrate LJ (shifted) */
+    double gamma;          /* drag coefficient of the dissipative coupling */
+    double xi;             /* solvation strength: F = xi grad C */
+    double mu, gamma_t;    /* substrate friction: |F_t| = min(gamma_t |v_t|, mu N) */
+    double bead_mass;
+    int substeps;          /* MD sub-steps per LB step (paper: 5) */
+    int max_beads;         /* bead capacity of this instance */
+    double rcon;           /* contact cut-off of the network model (paper: 2.1) */
+    double x_src, x_snk;   /* electrodes: beads with x < x_src / x > x_snk */
+    uint64_t seed;         /* seed of lbm_add_nanowires' random placement */
+} lbm_config;
+
+typedef struct lbm_descriptors {
+    double S_x;            /* mean over bonds of 2 cos^2(zeta_x) - 1 (Eq. (13), one bin) */
+    int n_clusters;        /* connected components of bonds + contacts r < rcon */
+    int percolates;        /* 1 if one component touches both electrodes */
+    int n_beads, n_bonds;
+    double mass_R, mass_B; /* total populations of each component (FP64 sums) */
+    double evaporated;     /* total mass converted liquid -> gas */
+    double top_in, top_out;/* total mass that entered / left through the top plane */
+    double h0;             /* maximum liquid column height at the first evaporating step */
+    long long step;        /* steps taken */
+} lbm_descriptors;
+
+/* Field ids of lbm_read_fields / lbm_write_fields.  Every field moves as FP64
+ * on the host side except LBM_FIELD_BEAD_TOPO (int32). */
+enum {
+    LBM_FIELD_POPULATIONS = 1, /* [2][19][nz][ny][nx]: post-collision f^R, then f^B (rw) */
+    LBM_FIELD_MOMENTS = 2,     /* [nz][ny][nx][5]: rho_R, rho_B, j_x, j_y, j_z of the
+                                  streamed populations of the next step (r) */
+    LBM_FIELD_COLOUR = 3,      /* [nz][ny][nx]: C of the next step (r) */
+    LBM_FIELD_BEAD_X = 4,      /* [n_beads][3] positions (rw) */
+    LBM_FIELD_BEAD_V = 5,      /* [n_beads][3] velocities (rw) */
+    LBM_FIELD_BEAD_F = 6,      /* [n_beads][3] force of the last sub-step (rw) */
+    LBM_FIELD_BEAD_TOPO = 7,   /* int32 [n_beads][2]: filament id, index in filament (r) */
+    LBM_FIELD_ACCUM = 8,       /* [6]: step, h0, evaporated, top_in, top_out, n_beads (rw) */
+    LBM_FIELD_FEXT = 9,        /* [nz][ny][nx][3]: force the beads put on the fluid in
+                                  the last step (r; zero where no bead is near) */
+    LBM_FIELD_THETA_COT = 10   /* [ny][nx]: cot(theta) of the substrate (r) */
+};
+
+typedef struct lbm_handle lbm_handle;
+
+/* Bytes of device workspace needed by lbm_create() for these instances. */
+size_t lbm_workspace_bytes(const lbm_config* cfgs, int n_instances);
+
+/* Build a handle over caller-owned device memory `dev_ws` (ws_bytes long,
+ * 16-byte aligned) working on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  Validates every config, lays out the workspace,
+ * initialises each droplet at rest in equilibrium and the derived moment
+ * buffers.  On error *out is NULL and nothing is kept. */
+lbm_status lbm_create(const lbm_config* cfgs, int n_instances, void* dev_ws, size_t ws_bytes,
+                      void* stream, lbm_handle** out);
+
+/* Contact-angle map of instance `inst`: theta_deg_xy[ny*nx] in degrees,
+ * 0 < theta < 180, measured through the liquid (Sec. II.A wetting model,
+ * Fig. 1 patch pattern).  Host array, copied. */
+lbm_status lbm_set_substrate_pattern(lbm_handle* h, int inst, const double* theta_deg_xy);
+
+/* Add n_wires straight filaments of length `length` (n_b = round(length/d0)
+ * beads spaced d0, Sec. II.A).  centers/dirs are host arrays [n_wires][3];
+ * pass NULL for both to place them at random (seeded, uniform centres,
+ * isotropic directions, every bead where C > 0.9, beads of different
+ * filaments further apart than d0; Sec. III.B set-up).  Velocities and
+ * carried forces start at zero.  Fails with LBM_ECAPACITY past max_beads and
+ * LBM_EINVAL if random placement finds no room after many tries. */
+lbm_status lbm_add_nanowires(lbm_handle* h, int inst, int n_wires, double length,
+                             const double* centers, const double* dirs, uint64_t seed);
+
+/* Enqueue n_steps time steps of every instance on the handle's stream. */
+lbm_status lbm_step(lbm_handle* h, int n_steps);
+
+/* Measurement aid (the paper has no counterpart): advance n_steps like
+ * lbm_step() but with direct launches, recording CUDA events on the handle's
+ * stream around every fused fluid-kernel launch and around every whole step.
+ * Synchronises; *ms_fluid and *ms_step receive the mean milliseconds per
+ * fluid launch and per step. */
+lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, double* ms_step);
+
+/* Wait for the stream and return the first latched device-side failure. */
+lbm_status lbm_sync(lbm_handle* h);
+
+/* Reset the latched device-side failure word. */
+lbm_status lbm_clear_error(lbm_handle* h);
+
+/* Copy one field of instance `inst` to host memory (layouts above);
+ * `bytes` must equal the field's size.  Synchronises the stream. */
+lbm_status lbm_read_fields(lbm_handle* h, int inst, unsigned field, void* host_dst, size_t bytes);
+
+/* Overwrite one writable field from host memory (checkpoint restore).
+ * Writing populations recomputes the derived moment buffers.  Synchronous. */
+lbm_status lbm_write_fields(lbm_handle* h, int inst, unsigned field, const void* host_src,
+                            size_t bytes);
+
+/* Deposit descriptors of instance `inst` (Sec. II.B): nematic order, contact
+ * clusters, percolation between the electrodes, plus mass budgets.
+ * Synchronises the stream. */
+lbm_status lbm_deposit_descriptors(lbm_handle* h, int inst, lbm_descriptors* out);
+
+/* Release the handle (the workspace stays the caller's). */
+lbm_status lbm_destroy(lbm_handle* h);
+
+const char* lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,498 @@
+// Filament kernels: bead-spring chains (Eqs. (9)-(12)) coupled to the fluid
+// by a dissipative drag with equal and opposite reaction (Sec. II.A,
+// Ahlrichs-Duenweg scheme), a solvation force xi grad C, substrate adhesion
+// and load-dependent friction; `substeps` velocity-Verlet sub-steps per LB
+// step on a frozen fluid.  Beads are FP64 throughout.
+#pragma once
+
+#include "kernels_fluid.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ double min_image(double d, int L) { return d - L * floor(d / L + 0.5); }
+
+// (d0/r)^12 - 2 (d0/r)^6 and its r-derivative (Eq. (12) without prefactor)
+__device__ __forceinline__ double lj_shape(double d0, double r) {
+    const double s = d0 / r, s2 = s * s, s6 = s2 * s2 * s2;
+    return s6 * s6 - 2.0 * s6;
+}
+__device__ __forceinline__ double lj_shape_dr(double d0, double r) {
+    const double s = d0 / r, s2 = s * s, s6 = s2 * s2 * s2;
+    return (-12.0 * s6 * s6 + 12.0 * s6) / r;
+}
+
+// dU/dr of a bead pair; `sep` = |index difference| if same filament, else 0
+__device__ __forceinline__ double pair_dUdr(const InstDev& I, bool same, int sep, double r, int& err) {
+    double f = 0.0;
+    if (same && sep == 1) {  // FENE, Eq. (9)
+        double q = r * r / (I.Rm * I.Rm);
+        if (q >= 1.0) {
+            err |= ERR_FENE;
+            q = 0.99;
+        }
+        f += I.ks * r / (1.0 - q);
+    }
+    if (same && sep == 2) f += I.kb * (r - 2.0 * I.d0);  // bending, Eq. (11)
+    if (r <= I.d0) f += I.eps_wca * lj_shape_dr(I.d0, r);  // WCA, Eq. (10)
+    if (!same && I.eps_coh > 0.0 && r > I.d0 && r < I.rc) f += I.eps_coh * lj_shape_dr(I.d0, r);
+    return f;
+}
+
+// trilinear stencil around a position (z clamped into the fluid)
+__device__ __forceinline__ void stencil(const InstDev& I, const double* X, long long* id, double* w) {
+    // a non-finite position (already an error) is mapped to the origin so that
+    // no index is ever formed from it
+    double px = X[0], py = X[1], pz = X[2];
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) px = py = pz = 0.0;
+    px -= I.nx * floor(px / I.nx);
+    py -= I.ny * floor(py / I.ny);
+    pz = pz < 0.0 ? 0.0 : (pz > I.nz - 1 ? (double)(I.nz - 1) : pz);
+    const int x0 = min((int)floor(px), I.nx - 1), y0 = min((int)floor(py), I.ny - 1);
+    int z0 = (int)floor(pz);
+    if (I.nz >= 2 && z0 > I.nz - 2) z0 = I.nz - 2;
+    const double fx = px - x0, fy = py - y0, fz = pz - z0;
+    const int z1 = I.nz >= 2 ? z0 + 1 : z0;
+    int k = 0;
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                const int xx = wrapi(x0 + a, I.nx), yy = wrapi(y0 + b, I.ny), zz = c ? z1 : z0;
+                id[k] = ((long long)zz * I.ny + yy) * I.nx + xx;
+                w[k] = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy) * (c ? fz : 1.0 - fz);
+                ++k;
+            }
+}
+
+__device__ __forceinline__ long long tile_of(const InstDev& I, long long node) {
+    const int x = (int)(node % I.nx), y = (int)((node / I.nx) % I.ny),
+              z = (int)(node / ((long long)I.nx * I.ny));
+    return ((long long)(z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
+}
+
+// Step start: remember positions, flag the coupling tiles around every bead.
+__global__ void k_bead_begin(const InstDev* __restrict__ insts) {
+    const InstDev& I = insts[blockIdx.y];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= I.nb) return;
+    double X[3];
+    for (int d = 0; d < 3; ++d) X[d] = I.bx0[3 * a + d] = I.bx[3 * a + d];
+    if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]))) {
+        atomicOr(I.err, ERR_BEAD);
+        return;
+    }
+    X[2] = X[2] < -1.0 ? -1.0 : (X[2] > I.nz ? (double)I.nz : X[2]);
+    const int fx = wrapi((int)floor(X[0] - I.nx * floor(X[0] / I.nx)), I.nx);
+    const int fy = wrapi((int)floor(X[1] - I.ny * floor(X[1] / I.ny)), I.ny);
+    const int fz = (int)floor(X[2]);
+    int t8z[4], nzt = 0;
+    for (int dz = -1; dz <= 2; ++dz) {
+        int z = fz + dz;
+        z = z < 0 ? 0 : (z >= I.nz ? I.nz - 1 : z);
+        const int t = z >> 3;
+        bool seen = false;
+        for (int k = 0; k < nzt; ++k) seen |= t8z[k] == t;
+        if (!seen) t8z[nzt++] = t;
+    }
+    for (int dy = -1; dy <= 2; ++dy)
+        for (int dx = -1; dx <= 2; ++dx) {
+            const int x = wrapi(fx + dx, I.nx), y = wrapi(fy + dy, I.ny);
+            for (int k = 0; k < nzt; ++k)
+                I.tflag[((long long)t8z[k] * I.t8y + (y >> 3)) * I.t8x + (x >> 3)] = 1;
+        }
+}
+
+// u* = (j + (F_s + body)/2)/rho and grad C on the nodes of flagged tiles.
+template <class S>
+__global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ insts,
+                                                    const StepGlobals* __restrict__ glob) {
+    using T = typename S::T;
+    using E = typename S::E;
+    const InstDev& I = insts[blockIdx.y];
+    const int ntile = I.t8x * I.t8y * I.t8z;
+    const int t = blockIdx.x;
+    if (t >= ntile || I.tflag == nullptr || !I.tflag[t] || I.nb == 0) return;
+    __shared__ T sC[12][12][12];
+    __shared__ T sN[10][10][10][3];
+    const long long step = __ldcg(&glob->step);
+    const T* rho = (const T*)I.rho[step % 3];
+    const E* src = (const E*)I.pop[step & 1];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N, cs = 19 * N;
+    const int X0 = (t % I.t8x) * 8, Y0 = ((t / I.t8x) % I.t8y) * 8, Z0 = (t / (I.t8x * I.t8y)) * 8;
+    const int tid = threadIdx.x;
+    for (int s = tid; s < 12 * 12 * 12; s += 512) {
+        const int lx = s % 12, ly = (s / 12) % 12, lz = s / 144;
+        const int z = Z0 - 2 + lz;
+        sC[lz][ly][lx] = (z < -1 || z > nz) ? T(0) : colour_ext<T>(I, rho, X0 - 2 + lx, Y0 - 2 + ly, z);
+    }
+    __syncthreads();
+    for (int s = tid; s < 1000; s += 512) {
+        const int lx = s % 10, ly = (s / 10) % 10, lz = s / 100;
+        const int z = Z0 - 1 + lz;
+        T* nn = sN[lz][ly][lx];
+        if (z < 0 || z >= nz) continue;
+        T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const T c = sC[lz + 1 + cz(i)][ly + 1 + cy(i)][lx + 1 + cx(i)];
+            const T w = (T)wq(i);
+            gx += w * cx(i) * c;
+            gy += w * cy(i) * c;
+            gz += w * cz(i) * c;
+        }
+        gx *= T(3);
+        gy *= T(3);
+        gz *= T(3);
+        const T g = sqrt(gx * gx + gy * gy + gz * gz);
+        if (g > T(1e-8)) {
+            nn[0] = gx / g;
+            nn[1] = gy / g;
+            nn[2] = gz / g;
+        } else {
+            nn[0] = nn[1] = nn[2] = T(0);
+        }
+    }
+    __syncthreads();
+    // normals outside the fluid copy the nearest fluid plane
+    for (int s = tid; s < 100; s += 512) {
+        const int lx = s % 10, ly = s / 10;
+        if (Z0 - 1 < 0)
+            for (int d = 0; d < 3; ++d) sN[0][ly][lx][d] = sN[1][ly][lx][d];
+        for (int lz = 0; lz < 10; ++lz)
+            if (Z0 - 1 + lz == nz)
+                for (int d = 0; d < 3; ++d) sN[lz][ly][lx][d] = sN[lz - 1][ly][lx][d];
+    }
+    __syncthreads();
+    const int lx = tid % 8, ly = (tid / 8) % 8, lz = tid / 64;
+    const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
+    if (x >= nx || y >= ny || z >= nz) return;
+    const long long node = ((long long)z * ny + y) * nx + x;
+    // the sub-steps of this step accumulate the drag reaction here from zero
+    T* fe = (T*)I.fext + 3 * node;
+    fe[0] = fe[1] = fe[2] = T(0);
+    T gx = 0, gy = 0, gz = 0, kap = 0;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const T c = sC[lz + 2 + cz(i)][ly + 2 + cy(i)][lx + 2 + cx(i)];
+        const T w = (T)wq(i);
+        gx += w * cx(i) * c;
+        gy += w * cy(i) * c;
+        gz += w * cz(i) * c;
+    }
+    gx *= T(3);
+    gy *= T(3);
+    gz *= T(3);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const T* nn = sN[lz + 1 + cz(i)][ly + 1 + cy(i)][lx + 1 + cx(i)];
+        kap += (T)wq(i) * (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]);
+    }
+    kap *= T(-3);
+    const T hs = T(0.5) * (T)I.sigma;
+    const T rho0 = (T)I.rho0;
+    T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sz = z - cz(i);
+        T r, b;
+        if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
+            S::load(src, cs, (long long)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
+        } else if (sz >= nz) {
+            r = T(0);
+            b = (T)wq(i) * rho0;
+        } else {
+            const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
+            S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i), rho0,
+                    r, b);
+        }
+        rR += r;
+        rB += b;
+        const T F = r + b;
+        jx += cx(i) * F;
+        jy += cy(i) * F;
+        jz += cz(i) * F;
+    }
+    const T rr = rR + rB;
+    T* u = (T*)I.ust + 3 * node;
+    T* g = (T*)I.gcol + 3 * node;
+    u[0] = (jx + T(0.5) * (hs * kap * gx + (T)I.body[0])) / rr;
+    u[1] = (jy + T(0.5) * (hs * kap * gy + (T)I.body[1])) / rr;
+    u[2] = (jz + T(0.5) * (hs * kap * gz + (T)I.body[2])) / rr;
+    g[0] = gx;
+    g[1] = gy;
+    g[2] = gz;
+}
+
+// Verlet neighbour list for the step: pairs closer than rlist that are not
+// bonded or bending partners (those are handled by index).
+__global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
+    const InstDev& I = insts[blockIdx.y];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= I.nb) return;
+    const double xa = I.bx[3 * a], ya = I.bx[3 * a + 1], za = I.bx[3 * a + 2];
+    const int fa = I.bfil[a], pa = I.bpos[a];
+    const double r2 = I.rlist * I.rlist;
+    int cnt = 0;
+    for (int b = 0; b < I.nb; ++b) {
+        if (b == a) continue;
+        if (I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2) continue;
+        const double dx = min_image(I.bx[3 * b] - xa, I.nx), dy = min_image(I.bx[3 * b + 1] - ya, I.ny),
+                     dz = I.bx[3 * b + 2] - za;
+        if (dx * dx + dy * dy + dz * dz < r2) {
+            if (cnt < I.max_nbr) I.nbr[(long long)a * I.max_nbr + cnt] = b;
+            ++cnt;
+        }
+    }
+    if (cnt > I.max_nbr) {
+        atomicOr(I.err, ERR_CAP);
+        cnt = I.max_nbr;
+    }
+    I.nnbr[a] = cnt;
+}
+
+// First half kick and drift of the step
+__global__ void k_bead_kickdrift(const InstDev* __restrict__ insts) {
+    const InstDev& I = insts[blockIdx.y];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= I.nb) return;
+    const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
+    double X[3];
+    for (int d = 0; d < 3; ++d) {
+        const double vh = I.bv[3 * a + d] + hk * I.bF[3 * a + d];
+        I.bvh[3 * a + d] = vh;
+        X[d] = I.bx[3 * a + d] + dt * vh;
+    }
+    X[0] -= I.nx * floor(X[0] / I.nx);
+    X[1] -= I.ny * floor(X[1] / I.ny);
+    if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) atomicOr(I.err, ERR_BEAD);
+    for (int d = 0; d < 3; ++d) I.bx2[3 * a + d] = X[d];
+}
+
+// Force evaluation of sub-step s (1-based) at the current positions with the
+// half-step velocities, second half kick, reaction onto the fluid, and (not
+// last) the next first half kick and drift.
+template <typename T>
+__global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
+    const InstDev& I = insts[blockIdx.y];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= I.nb) return;
+    const bool last = s == I.substeps;
+    const double* cur = (s & 1) ? I.bx2 : I.bx;
+    double* nxt = (s & 1) ? I.bx : I.bx2;
+    const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
+    int err = 0;
+    const double P[3] = {cur[3 * a], cur[3 * a + 1], cur[3 * a + 2]};
+    const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
+    const int fa = I.bfil[a], pa = I.bpos[a];
+    double f[3] = {0.0, 0.0, 0.0};
+    auto pair = [&](int b, bool same, int sep) {
+        double d[3] = {min_image(cur[3 * b] - P[0], I.nx), min_image(cur[3 * b + 1] - P[1], I.ny),
+                       cur[3 * b + 2] - P[2]};
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const double g = pair_dUdr(I, same, sep, r, err);
+        if (g != 0.0)
+            for (int k = 0; k < 3; ++k) f[k] += g * d[k] / r;
+    };
+    for (int k = -2; k <= 2; ++k) {
+        const int b = a + k;
+        if (k == 0 || b < 0 || b >= I.nb) continue;
+        if (I.bfil[b] == fa && I.bpos[b] - pa == k) pair(b, true, k < 0 ? -k : k);
+    }
+    const int nn = I.nnbr[a];
+    for (int k = 0; k < nn; ++k) {
+        const int b = I.nbr[(long long)a * I.max_nbr + k];
+        const bool same = I.bfil[b] == fa;
+        pair(b, same, same ? abs(I.bpos[b] - pa) : 0);
+    }
+    // fluid coupling: drag towards the local velocity and solvation along grad C
+    long long id[8];
+    double w[8];
+    stencil(I, P, id, w);
+    double u[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+    const T* ust = (const T*)I.ust;
+    const T* gcl = (const T*)I.gcol;
+    for (int k = 0; k < 8; ++k)
+        for (int d = 0; d < 3; ++d) {
+            u[d] += w[k] * (double)ust[3 * id[k] + d];
+            g[d] += w[k] * (double)gcl[3 * id[k] + d];
+        }
+    double drag[3];
+    for (int d = 0; d < 3; ++d) {
+        drag[d] = I.gamma * (u[d] - vh[d]);
+        f[d] += drag[d] + I.xi * g[d];
+    }
+    // substrate adhesion (LJ at the image distance) and load-dependent friction
+    const double rw = 2.0 * (P[2] + 0.5);
+    double fw = 0.0;
+    if (I.eps_s > 0.0 && rw < I.rc && rw > 0.0) fw = -2.0 * I.eps_s * lj_shape_dr(I.d0, rw);
+    if (I.eps_s > 0.0 && rw < I.rc) {
+        const double load = (f[2] < 0.0 ? -f[2] : 0.0) + (fw < 0.0 ? -fw : 0.0);
+        const double vt = sqrt(vh[0] * vh[0] + vh[1] * vh[1]);
+        if (vt > 0.0) {
+            double mag = I.gamma_t * vt;
+            if (mag > I.mu * load) mag = I.mu * load;
+            f[0] -= mag * vh[0] / vt;
+            f[1] -= mag * vh[1] / vt;
+        }
+    }
+    f[2] += fw;
+    // reaction of the drag onto the fluid, only inside flagged tiles
+    T* fe = (T*)I.fext;
+    for (int k = 0; k < 8; ++k) {
+        if (!I.tflag[tile_of(I, id[k])]) {
+            err |= ERR_BEAD;
+            continue;
+        }
+        for (int d = 0; d < 3; ++d) atomicAdd(fe + 3 * id[k] + d, (T)(-dt * w[k] * drag[d]));
+    }
+    double v[3];
+    for (int d = 0; d < 3; ++d) {
+        I.bF[3 * a + d] = f[d];
+        v[d] = vh[d] + hk * f[d];
+    }
+    if (!last) {
+        double X[3];
+        for (int d = 0; d < 3; ++d) {
+            const double v2 = v[d] + hk * f[d];
+            I.bvh[3 * a + d] = v2;
+            X[d] = P[d] + dt * v2;
+        }
+        X[0] -= I.nx * floor(X[0] / I.nx);
+        X[1] -= I.ny * floor(X[1] / I.ny);
+        if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) err |= ERR_BEAD;
+        for (int d = 0; d < 3; ++d) nxt[3 * a + d] = X[d];
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            I.bv[3 * a + d] = v[d];
+            if (cur != I.bx) I.bx[3 * a + d] = P[d];
+        }
+        const double dx = min_image(P[0] - I.bx0[3 * a], I.nx),
+                     dy = min_image(P[1] - I.bx0[3 * a + 1], I.ny), dz = P[2] - I.bx0[3 * a + 2];
+        if (dx * dx + dy * dy + dz * dz > 0.25) err |= ERR_BEAD;
+    }
+    if (err) atomicOr(I.err, err);
+}
+
+// ---------------------------------------------------------------------------
+// Deposit descriptors (Sec. II.B): contact graph edges, then one block per
+// instance labels components by min-label propagation with pointer jumping,
+// and reduces S_x, cluster count and percolation.
+// ---------------------------------------------------------------------------
+__global__ void k_desc_edges(const InstDev* __restrict__ insts, int only) {
+    const InstDev& I = insts[only];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= I.nb) return;
+    const double r2 = I.rcon * I.rcon;
+    for (int b = a + 1; b < I.nb; ++b) {
+        const bool bonded = I.bfil[b] == I.bfil[a] && abs(I.bpos[b] - I.bpos[a]) == 1;
+        const double dx = min_image(I.bx[3 * b] - I.bx[3 * a], I.nx),
+                     dy = min_image(I.bx[3 * b + 1] - I.bx[3 * a + 1], I.ny),
+                     dz = I.bx[3 * b + 2] - I.bx[3 * a + 2];
+        if (bonded || dx * dx + dy * dy + dz * dz < r2) {
+            const int e = atomicAdd(I.nedges, 1);
+            if (e < I.max_edges)
+                I.edges[e] = make_int2(a, b);
+            else
+                atomicOr(I.err, ERR_CAP);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_desc_solve(const InstDev* __restrict__ insts, int only) {
+    const InstDev& I = insts[only];
+    const int n = I.nb;
+    int* lab = I.lab;
+    int* srcf = I.lab + I.nb_max;
+    int* snkf = I.lab + 2 * I.nb_max;
+    const int ne = min(*I.nedges, I.max_edges);
+    __shared__ int changed;
+    __shared__ double sred[32];
+    __shared__ int ired[32][3];
+    const int tid = threadIdx.x;
+    for (int a = tid; a < n; a += blockDim.x) {
+        lab[a] = a;
+        srcf[a] = 0;
+        snkf[a] = 0;
+    }
+    __syncthreads();
+    int it = 0;
+    for (; it <= n + 1; ++it) {
+        if (tid == 0) changed = 0;
+        __syncthreads();
+        for (int e = tid; e < ne; e += blockDim.x) {
+            const int2 ed = I.edges[e];
+            const int la = lab[ed.x], lb = lab[ed.y];
+            if (la != lb) {
+                const int m = la < lb ? la : lb;
+                atomicMin(lab + ed.x, m);
+                atomicMin(lab + ed.y, m);
+                atomicMin(lab + la, m);
+                atomicMin(lab + lb, m);
+                changed = 1;
+            }
+        }
+        __syncthreads();
+        for (int a = tid; a < n; a += blockDim.x) {
+            int l = lab[a];
+            for (int k = 0; k < 64 && lab[l] < l; ++k) l = lab[l];
+            atomicMin(lab + a, l);
+        }
+        __syncthreads();
+        if (!changed) break;
+        __syncthreads();
+    }
+    if (it > n + 1 && tid == 0) atomicOr(I.err, ERR_TIMEOUT);
+    // resolve every label to its root
+    for (int a = tid; a < n; a += blockDim.x) {
+        int l = lab[a];
+        for (int k = 0; k < n && lab[l] != l; ++k) l = lab[l];
+        lab[a] = l;
+    }
+    __syncthreads();
+    double s = 0.0;
+    int nb = 0, nc = 0;
+    for (int a = tid; a < n; a += blockDim.x) {
+        if (lab[a] == a) ++nc;
+        if (I.bx[3 * a] < I.x_src) srcf[lab[a]] = 1;
+        if (I.bx[3 * a] > I.x_snk) snkf[lab[a]] = 1;
+        if (a + 1 < n && I.bfil[a + 1] == I.bfil[a] && I.bpos[a + 1] == I.bpos[a] + 1) {
+            const double dx = min_image(I.bx[3 * (a + 1)] - I.bx[3 * a], I.nx),
+                         dy = min_image(I.bx[3 * (a + 1) + 1] - I.bx[3 * a + 1], I.ny),
+                         dz = I.bx[3 * (a + 1) + 2] - I.bx[3 * a + 2];
+            s += 2.0 * dx * dx / (dx * dx + dy * dy + dz * dz) - 1.0;
+            ++nb;
+        }
+    }
+    __syncthreads();
+    int perc = 0;
+    for (int a = tid; a < n; a += blockDim.x) perc |= (srcf[a] && snkf[a]);
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+        perc |= __shfl_xor_sync(0xffffffffu, perc, o);
+    }
+    if ((tid & 31) == 0) {
+        sred[tid >> 5] = s;
+        ired[tid >> 5][0] = nb;
+        ired[tid >> 5][1] = nc;
+        ired[tid >> 5][2] = perc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double ss = 0.0;
+        int b = 0, c = 0, p = 0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+            ss += sred[w];
+            b += ired[w][0];
+            c += ired[w][1];
+            p |= ired[w][2];
+        }
+        I.desc[0] = b ? ss / b : 0.0;
+        I.desc[1] = c;
+        I.desc[2] = p;
+        I.desc[3] = b;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,563 @@
+// Fluid kernels: one fused pass per time step (pull-stream, moments, CSF,
+// forced BGK, recolouring, evaporation, store, push of the next moments),
+// plus initialisation, moment recomputation and diagnostics.
+// Method: Sec. II.A of "Evaporation-Driven Nanowire Self-Assembly in an
+// Elongated Droplet" (Eqs. (1)-(3), (8) and the colour-gradient / CSF /
+// wetting paragraphs).
+#pragma once
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+template <typename T>
+__device__ __forceinline__ T colour_of(const T* __restrict__ rho, long long N, long long n) {
+    T a = rho[n], b = rho[N + n];
+    return (a - b) / (a + b);
+}
+
+// Wetting ghost layer below z = 0 (Sec. II.A, Akai's geometric scheme on a
+// flat wall): C(x,y,-1) = C(x,y,0) + cot(theta) |grad_par C(x,y,0)|, clipped
+// to [-1, 1]; grad_par with the isotropic 2-D weights 4/9, 1/9, 1/36.
+template <typename T>
+__device__ T ghost_colour(const InstDev& I, const T* __restrict__ rho, int x, int y) {
+    const int nx = I.nx, ny = I.ny;
+    const long long N = I.N;
+    T gx = 0, gy = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int k = (dx != 0) + (dy != 0);
+            const T w = k == 0 ? T(4.0 / 9.0) : (k == 1 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+            const T c = colour_of(rho, N, (long long)wrapi(y + dy, ny) * nx + wrapi(x + dx, nx));
+            gx += w * dx * c;
+            gy += w * dy * c;
+        }
+    gx *= T(3);
+    gy *= T(3);
+    T g = colour_of(rho, N, (long long)y * nx + x) + (T)I.cot[y * nx + x] * sqrt(gx * gx + gy * gy);
+    return g > T(1) ? T(1) : (g < T(-1) ? T(-1) : g);
+}
+
+// Colour at an extended position: z = -1 is the ghost layer, z = nz copies the top plane.
+template <typename T>
+__device__ T colour_ext(const InstDev& I, const T* __restrict__ rho, int x, int y, int z) {
+    x = wrapi(x, I.nx);
+    y = wrapi(y, I.ny);
+    if (z < 0) return ghost_colour<T>(I, rho, x, y);
+    if (z >= I.nz) z = I.nz - 1;
+    return colour_of(rho, I.N, ((long long)z * I.ny + y) * I.nx + x);
+}
+
+// ---------------------------------------------------------------------------
+// Fused time step over one tile (TX x TY columns, planes z0..z1-1), marching
+// upwards in z.  Shared memory holds a 3-plane ring of C with a 2-cell halo,
+// a 3-plane ring of unit normals with a 1-cell halo, the core gradient of the
+// next two planes, and a 3-plane ring of moment accumulators with a 1-cell
+// halo into which every stored population is pushed to the node it streams
+// to next step.  Fully interior nodes are stored plainly; tile-edge and halo
+// nodes are added atomically (their buffer was zeroed one step earlier).
+// ---------------------------------------------------------------------------
+template <class S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+    k_stream_collide(const InstDev* __restrict__ insts, const TileDesc* __restrict__ tiles,
+                     StepGlobals* __restrict__ glob) {
+    using T = typename S::T;
+    using E = typename S::E;
+    constexpr int NT = TX * TY;
+    constexpr int HX2 = TX + 4, HY2 = TY + 4, HX1 = TX + 2, HY1 = TY + 2;
+    __shared__ T sC[3][HY2][HX2];
+    __shared__ T sN[3][HY1][HX1][3];
+    __shared__ T sG[2][TY][TX][3];
+    __shared__ T sA[3][HY1][HX1][2];
+    __shared__ double sRed[NT / 32][3];
+    __shared__ int sErr;
+
+    const TileDesc td = tiles[blockIdx.x];
+    const InstDev& I = insts[td.inst];
+    const int nx = I.nx, ny = I.ny, nz = I.nz, top_bc = I.top_bc;
+    const long long N = I.N;
+    const long long cs = 19 * N;
+    const long long step = __ldcg(&glob->step);
+    const int pa = (int)(step & 1);
+    const int pr = (int)(step % 3);
+    const E* __restrict__ src = (const E*)I.pop[pa];
+    E* __restrict__ dst = (E*)I.pop[pa ^ 1];
+    const T* __restrict__ rho_r = (const T*)I.rho[pr];
+    T* __restrict__ rho_w = (T*)I.rho[(pr + 1) % 3];
+    T* __restrict__ rho_z = (T*)I.rho[(pr + 2) % 3];
+    T* __restrict__ fext = (T*)I.fext;
+    const unsigned char* __restrict__ tflag = I.tflag;
+
+    const int x0 = td.x0, y0 = td.y0, z0 = td.z0, z1 = td.z1;
+    const int tw = min(TX, nx - x0), th = min(TY, ny - y0);
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const bool active = tx < tw && ty < th;
+    const int x = x0 + tx, y = y0 + ty;
+
+    const T rho0 = (T)I.rho0, tauR = (T)I.tau_R, tauB = (T)I.tau_B, beta = (T)I.beta;
+    const T hsig = T(0.5) * (T)I.sigma;
+    const T bfx = (T)I.body[0], bfy = (T)I.body[1], bfz = (T)I.body[2];
+    const bool evap_on = I.J0 > 0.0 && I.evap_start >= 0 && step >= I.evap_start && I.acc[1] > 0.0;
+    const T J0 = (T)I.J0, Kk = (T)I.K, inv_h0 = evap_on ? (T)(1.0 / I.acc[1]) : T(0);
+
+    auto ring = [](int q) { return ((q % 3) + 3) % 3; };
+
+    // liquid column height of this thread's column, h = sum_z (1+C)/2 (Eq. (8))
+    T hcol = 0;
+    if (evap_on && active) {
+        for (int z = 0; z < nz; ++z) {
+            const long long n = ((long long)z * ny + y) * nx + x;
+            hcol += (T(1) + colour_of(rho_r, N, n)) / T(2);
+        }
+    }
+
+    for (int s = tid; s < 3 * HY1 * HX1 * 2; s += NT) (&sA[0][0][0][0])[s] = T(0);
+    if (tid == 0) sErr = 0;
+
+    // C of plane p into the ring, over the window of the tile plus 2 cells
+    auto loadC = [&](int p) {
+        if (p < -1 || p > nz) return;
+        const int r = ring(p);
+        for (int s = tid; s < HX2 * HY2; s += NT) {
+            const int sy = s / HX2, sx = s % HX2;
+            if (sx > tw + 3 || sy > th + 3) continue;
+            sC[r][sy][sx] = colour_ext<T>(I, rho_r, x0 - 2 + sx, y0 - 2 + sy, p);
+        }
+    };
+    // gradient and unit normal of plane q over the tile plus 1 cell
+    auto computeN = [&](int q) {
+        const int rq = ring(q);
+        if (q >= 0 && q < nz) {
+            const int rm = ring(q - 1), r0 = ring(q), rp = ring(q + 1);
+            for (int s = tid; s < HX1 * HY1; s += NT) {
+                const int sy = s / HX1, sx = s % HX1;
+                if (sx > tw + 1 || sy > th + 1) continue;
+                T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+                for (int i = 1; i < 19; ++i) {
+                    const int rr = cz(i) < 0 ? rm : (cz(i) > 0 ? rp : r0);
+                    const T c = sC[rr][sy + 1 + cy(i)][sx + 1 + cx(i)];
+                    const T w = (T)wq(i);
+                    gx += w * cx(i) * c;
+                    gy += w * cy(i) * c;
+                    gz += w * cz(i) * c;
+                }
+                gx *= T(3);
+                gy *= T(3);
+                gz *= T(3);
+                const T g = sqrt(gx * gx + gy * gy + gz * gz);
+                if (g > T(1e-8)) {
+                    sN[rq][sy][sx][0] = gx / g;
+                    sN[rq][sy][sx][1] = gy / g;
+                    sN[rq][sy][sx][2] = gz / g;
+                } else {
+                    sN[rq][sy][sx][0] = sN[rq][sy][sx][1] = sN[rq][sy][sx][2] = T(0);
+                }
+                if (sx >= 1 && sx <= tw && sy >= 1 && sy <= th) {
+                    T* G = sG[q & 1][sy - 1][sx - 1];
+                    G[0] = gx;
+                    G[1] = gy;
+                    G[2] = gz;
+                }
+            }
+        } else if (q == -1 || q == nz) {
+            // outside the fluid the normal copies the nearest fluid plane
+            const int rf = ring(q == -1 ? 0 : nz - 1);
+            for (int s = tid; s < HX1 * HY1 * 3; s += NT) (&sN[rq][0][0][0])[s] = (&sN[rf][0][0][0])[s];
+        }
+    };
+
+    double evap_sum = 0.0, top_in = 0.0, top_out = 0.0;
+    int err = 0;
+
+    // push a post-collision pair into the accumulator ring
+    auto push = [&](int sx, int sy, int q, T r, T b) {
+        T* a = sA[ring(q)][sy][sx];
+        atomicAdd(a, r);
+        atomicAdd(a + 1, b);
+    };
+
+    // flush the completed accumulator plane q to global memory
+    auto flush = [&](int q) {
+        const int r = ring(q);
+        for (int s = tid; s < HX1 * HY1; s += NT) {
+            const int sy = s / HX1, sx = s % HX1;
+            if (sx > tw + 1 || sy > th + 1) continue;
+            const T a0 = sA[r][sy][sx][0], a1 = sA[r][sy][sx][1];
+            sA[r][sy][sx][0] = T(0);
+            sA[r][sy][sx][1] = T(0);
+            if (q < 0 || q >= nz) continue;
+            const int gx = wrapi(x0 - 1 + sx, nx), gy = wrapi(y0 - 1 + sy, ny);
+            const long long n = ((long long)q * ny + gy) * nx + gx;
+            const bool core = sx >= 1 && sx <= tw && sy >= 1 && sy <= th && q >= z0 && q < z1;
+            const bool interior = core && sx > 1 && sx < tw && sy > 1 && sy < th &&
+                                  !(q == z0 && z0 > 0) && !(q == z1 - 1 && z1 < nz);
+            if (interior) {
+                rho_w[n] = a0;
+                rho_w[N + n] = a1;
+            } else {
+                atomicAdd(rho_w + n, a0);
+                atomicAdd(rho_w + N + n, a1);
+                if (core) {
+                    rho_z[n] = T(0);
+                    rho_z[N + n] = T(0);
+                }
+            }
+        }
+    };
+
+    // ---- prologue: C planes and normals below the first plane ----
+    if (z0 == 0) {
+        loadC(-1);
+        loadC(0);
+        loadC(1);
+        __syncthreads();
+        computeN(0);
+        __syncthreads();
+        computeN(-1);
+        __syncthreads();
+    } else {
+        loadC(z0 - 2);
+        loadC(z0 - 1);
+        loadC(z0);
+        __syncthreads();
+        computeN(z0 - 1);
+        __syncthreads();
+        loadC(z0 + 1);
+        __syncthreads();
+        computeN(z0);
+        __syncthreads();
+    }
+
+    for (int z = z0; z < z1; ++z) {
+        loadC(z + 2);
+        __syncthreads();
+        computeN(z + 1);
+        __syncthreads();
+
+        if (active) {
+            const long long node = ((long long)z * ny + y) * nx + x;
+            // curvature kappa = -3 sum_i w_i c_i . n(x + c_i)
+            T kap = 0;
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const T* nn = sN[ring(z + cz(i))][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                kap += (T)wq(i) * (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]);
+            }
+            kap *= T(-3);
+            const T* G = sG[z & 1][ty][tx];
+            const T Gx = G[0], Gy = G[1], Gz = G[2];
+            T Fx = hsig * kap * Gx + bfx, Fy = hsig * kap * Gy + bfy, Fz = hsig * kap * Gz + bfz;
+            if (tflag != nullptr &&
+                tflag[((z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3)]) {
+                const T* fe = fext + 3 * node;
+                Fx += fe[0];
+                Fy += fe[1];
+                Fz += fe[2];
+            }
+
+            // pull-stream with half-way bounce-back at the wall and the gas plane on top
+            T Fi[19];
+            T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                const int sz = z - cz(i);
+                T r, b;
+                if (sz < 0 || (sz >= nz && top_bc == 0)) {
+                    S::load(src, cs, (long long)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
+                } else if (sz >= nz) {
+                    r = T(0);
+                    b = (T)wq(i) * rho0;
+                    top_in += (double)b;
+                } else {
+                    const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
+                    S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx,
+                            (T)wq(i), rho0, r, b);
+                }
+                rR += r;
+                rB += b;
+                Fi[i] = r + b;
+                jx += cx(i) * Fi[i];
+                jy += cy(i) * Fi[i];
+                jz += cz(i) * Fi[i];
+            }
+            if (z == nz - 1 && top_bc == 1) {
+                // what left the domain through the top in this stream
+#pragma unroll
+                for (int i = 0; i < 19; ++i)
+                    if (cz(i) > 0) {
+                        T r, b;
+                        S::load(src, cs, (long long)i * N + node, (T)wq(i), rho0, r, b);
+                        top_out += (double)r + (double)b;
+                    }
+            }
+
+            const T rho = rR + rB;
+            if (!(rho > T(0))) err |= ERR_NAN;
+            const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho,
+                    uz = (jz + T(0.5) * Fz) / rho;
+            const T omega = (rR / rho) / tauR + (rB / rho) / tauB;
+            const T usq = ux * ux + uy * uy + uz * uz;
+            const T uF = ux * Fx + uy * Fy + uz * Fz;
+            const T gsrc = T(1) - T(0.5) * omega;
+            const T gm = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
+            const bool hasg = gm > T(1e-8);
+            const T ig = hasg ? T(1) / gm : T(0);
+            const T phi = rR / rho;
+            const T coef = beta * (rR * rB / rho);
+            T dm = 0;
+            if (evap_on) {
+                const T ht = hcol * inv_h0;
+                if (ht > T(0)) dm = J0 / (Kk + ht) * T(0.5) * gm;
+            }
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                const T w = (T)wq(i);
+                const T cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+                const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+                const T cF = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
+                const T Sg = gsrc * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+                const T post = Fi[i] - omega * (Fi[i] - feq) + Sg;
+                const T cph = (i > 0 && hasg)
+                                  ? (cx(i) * Gx + cy(i) * Gy + cz(i) * Gz) * (T)inv_len(i) * ig
+                                  : T(0);
+                T r = phi * post + coef * w * cph;
+                T b = post - r;
+                if (i == 0 && evap_on) {
+                    T d = dm > r ? r : dm;
+                    d = d < T(0) ? T(0) : d;
+                    r -= d;
+                    b += d;
+                    evap_sum += (double)d;
+                }
+                T rq, bq;
+                S::store(dst, cs, (long long)i * N + node, w, rho0, r, b, rq, bq);
+                const int tz = z + cz(i);
+                if (tz < 0 || (tz >= nz && top_bc == 0)) {
+                    push(tx + 1, ty + 1, z, rq, bq);  // bounces back to this node
+                } else if (tz < nz) {
+                    push(tx + 1 + cx(i), ty + 1 + cy(i), tz, rq, bq);
+                }
+            }
+            if (z == nz - 1 && top_bc == 1) {
+                // gas inflow that the next stream brings to this node
+                T inB = 0;
+#pragma unroll
+                for (int i = 0; i < 19; ++i)
+                    if (cz(i) < 0) inB += (T)wq(i) * rho0;
+                push(tx + 1, ty + 1, z, T(0), inB);
+            }
+        }
+        __syncthreads();
+        flush(z - 1);
+    }
+    __syncthreads();
+    flush(z1 - 1);
+    __syncthreads();
+    flush(z1);
+
+    // ---- block sums of the FP64 budgets ----
+    double v[3] = {evap_sum, top_in, top_out};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((tid & 31) == 0)
+        for (int k = 0; k < 3; ++k) sRed[tid >> 5][k] = v[k];
+    if (err) atomicOr(&sErr, err);
+    __syncthreads();
+    if (tid < 3) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += sRed[w][tid];
+        if (s != 0.0) atomicAdd(I.acc + 2 + tid, s);
+    }
+    if (tid == 0) {
+        if (sErr) atomicOr(I.err, sErr);
+        // the last block to finish advances the step counter
+        __threadfence();
+        const unsigned t = atomicAdd(&glob->done, 1u);
+        if (t == gridDim.x - 1) {
+            glob->done = 0u;
+            glob->step = step + 1;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Moments of the streamed populations (pull + sum), used after initialisation
+// and after populations are written from the host.  Writes rho[pr] (both
+// components) and clears the next buffer.
+// ---------------------------------------------------------------------------
+template <class S>
+__global__ void k_moments(InstDev I, long long step, long long n0, long long len,
+                          double* __restrict__ diag) {
+    using T = typename S::T;
+    using E = typename S::E;
+    const long long N = I.N;
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= len) return;
+    const long long n = n0 + u;
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    const E* src = (const E*)I.pop[step & 1];
+    const long long cs = 19 * N;
+    const T rho0 = (T)I.rho0;
+    T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sz = z - cz(i);
+        T r, b;
+        if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
+            S::load(src, cs, (long long)opp(i) * N + n, (T)wq(opp(i)), rho0, r, b);
+        } else if (sz >= nz) {
+            r = T(0);
+            b = (T)wq(i) * rho0;
+        } else {
+            const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
+            S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i),
+                    rho0, r, b);
+        }
+        rR += r;
+        rB += b;
+        const T F = r + b;
+        jx += cx(i) * F;
+        jy += cy(i) * F;
+        jz += cz(i) * F;
+    }
+    if (diag) {
+        double* d = diag + 5 * u;
+        d[0] = rR;
+        d[1] = rB;
+        d[2] = jx;
+        d[3] = jy;
+        d[4] = jz;
+        return;
+    }
+    T* rho = (T*)I.rho[step % 3];
+    rho[n] = rR;
+    rho[N + n] = rB;
+    T* nxt = (T*)I.rho[(step + 1) % 3];
+    nxt[n] = T(0);
+    nxt[N + n] = T(0);
+    T* nn = (T*)I.rho[(step + 2) % 3];
+    nn[n] = T(0);
+    nn[N + n] = T(0);
+}
+
+// Initial droplet at rest in equilibrium: C = tanh(-(q-1) min(a,b,c)/width).
+template <class S>
+__global__ void k_init_droplet(InstDev I, int shape, double cx_, double cy_, double cz_, double a,
+                               double b, double c, double width) {
+    using E = typename S::E;
+    const long long N = I.N;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int nx = I.nx, ny = I.ny;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    double m = a < b ? a : b;
+    m = m < c ? m : c;
+    const double dx = (x - cx_) / a, dy = (y - cy_) / b, dz = (z - cz_) / c;
+    double q;
+    if (shape == 0) {
+        q = sqrt(dx * dx + dy * dy + dz * dz);
+    } else {
+        const double r = sqrt(dy * dy + dz * dz);
+        q = fabs(dx) > r ? fabs(dx) : r;
+    }
+    const double C = tanh(-(q - 1.0) * m / width);
+    E* p = (E*)I.pop[0];
+    for (int i = 0; i < 19; ++i)
+        S::from_f64(p, 19 * N, (long long)i * N + n, i, I.rho0, wq(i) * I.rho0 * (1.0 + C) / 2.0,
+                    wq(i) * I.rho0 * (1.0 - C) / 2.0);
+}
+
+// Populations <-> FP64 staging: elements t0..t0+len of [19][N]; staging
+// holds len values of f^R followed by len values of f^B.
+template <class S>
+__global__ void k_pop_to_f64(InstDev I, long long step, long long t0, long long len,
+                             double* __restrict__ out) {
+    using E = typename S::E;
+    const long long N = I.N;
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= len) return;
+    const long long t = t0 + u;
+    double r, b;
+    S::to_f64((const E*)I.pop[step & 1], 19 * N, t, (int)(t / N), I.rho0, r, b);
+    out[u] = r;
+    out[len + u] = b;
+}
+template <class S>
+__global__ void k_pop_from_f64(InstDev I, long long step, long long t0, long long len,
+                               const double* __restrict__ in) {
+    using E = typename S::E;
+    const long long N = I.N;
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= len) return;
+    const long long t = t0 + u;
+    S::from_f64((E*)I.pop[step & 1], 19 * N, t, (int)(t / N), I.rho0, in[u], in[len + u]);
+}
+
+// Colour field of the next step, FP64
+template <typename T>
+__global__ void k_colour(InstDev I, long long step, long long n0, long long len,
+                         double* __restrict__ out) {
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= len) return;
+    out[u] = (double)colour_of((const T*)I.rho[step % 3], I.N, n0 + u);
+}
+
+// Bead force on the fluid, FP64 copy of a node range
+template <typename T>
+__global__ void k_fext(InstDev I, long long n0, long long len, double* __restrict__ out) {
+    const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (u >= 3 * len || I.fext == nullptr) return;
+    const long long n = n0 + u / 3;
+    const int x = (int)(n % I.nx), y = (int)((n / I.nx) % I.ny), z = (int)(n / ((long long)I.nx * I.ny));
+    const bool live = I.tflag[((long long)(z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3)] != 0;
+    out[u] = live ? (double)((const T*)I.fext)[3 * n0 + u] : 0.0;
+}
+
+// Liquid column heights and their maximum -> h0 (first evaporating step)
+template <typename T>
+__global__ void k_h0(InstDev I, long long step) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncol = I.nx * I.ny;
+    double h = 0.0;
+    if (c < ncol) {
+        const T* rho = (const T*)I.rho[step % 3];
+        T s = 0;
+        for (int z = 0; z < I.nz; ++z) s += (T(1) + colour_of(rho, I.N, (long long)z * ncol + c)) / T(2);
+        h = (double)s;
+    }
+    for (int o = 16; o > 0; o >>= 1) h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+    if ((threadIdx.x & 31) == 0 && h > 0.0)
+        atomicMax((unsigned long long*)(I.acc + 1), (unsigned long long)__double_as_longlong(h));
+}
+
+// Component masses: sums of all stored populations (FP64 block sums)
+template <class S>
+__global__ void k_mass(InstDev I, long long step, double* __restrict__ out) {
+    using E = typename S::E;
+    const long long N = I.N;
+    double sr = 0.0, sb = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 19 * N;
+         t += (long long)gridDim.x * blockDim.x) {
+        double r, b;
+        S::to_f64((const E*)I.pop[step & 1], 19 * N, t, (int)(t / N), I.rho0, r, b);
+        sr += r;
+        sb += b;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, sr);
+        atomicAdd(out + 1, sb);
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,950 @@
+// Host side of the C ABI declared in include/lbm.h: configuration checks,
+// workspace layout over caller-owned device memory, launch sequence of one
+// time step (captured once into a CUDA graph and replayed), field transfer,
+// nanowire placement and descriptors.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <random>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "kernels_beads.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+constexpr int MAX_NBR = 64;
+constexpr size_t STAGE_BYTES = size_t(64) << 20;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int elem_bytes(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
+int comp_bytes(int prec) { return prec == LBM_FP64 ? 8 : 4; }
+
+// A bump allocator over the workspace; with base == nullptr it only measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    void* take(size_t bytes) {
+        off = align_up(off, 256);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+struct Layout {
+    std::vector<InstDev> inst;
+    StepGlobals* glob = nullptr;
+    InstDev* d_inst = nullptr;
+    TileDesc* d_tiles = nullptr;
+    double* stage = nullptr;
+    size_t stage_bytes = 0;
+    int ntiles = 0;
+};
+
+int chunk_z(const lbm_config& c) {
+    // z-chunk of the fused kernel: enough blocks to fill the GPU on small lattices
+    const long long cols = (long long)((c.nx + TILE_X - 1) / TILE_X) * ((c.ny + TILE_Y - 1) / TILE_Y);
+    int ch = c.nz;
+    while (cols * ((c.nz + ch - 1) / ch) < 4 * 148 && ch > 8) ch = (ch + 1) / 2;
+    return std::max(2, std::min(ch, c.nz));
+}
+
+std::vector<TileDesc> make_tiles(const lbm_config* cfgs, int n) {
+    std::vector<TileDesc> t;
+    for (int k = 0; k < n; ++k) {
+        const lbm_config& c = cfgs[k];
+        const int ch = chunk_z(c);
+        std::vector<std::pair<int, int>> zr;
+        for (int z0 = 0; z0 < c.nz;) {
+            int z1 = std::min(c.nz, z0 + ch);
+            if (c.nz - z1 > 0 && c.nz - z1 < 2) z1 = c.nz;  // never leave a 1-plane chunk
+            zr.push_back({z0, z1});
+            z0 = z1;
+        }
+        for (auto& r : zr)
+            for (int y0 = 0; y0 < c.ny; y0 += TILE_Y)
+                for (int x0 = 0; x0 < c.nx; x0 += TILE_X)
+                    t.push_back(TileDesc{k, x0, y0, r.first, r.second, 0, 0, 0});
+    }
+    return t;
+}
+
+void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
+    L.inst.assign(n, InstDev{});
+    L.glob = (StepGlobals*)cv.take(sizeof(StepGlobals));
+    L.d_inst = (InstDev*)cv.take(sizeof(InstDev) * n);
+    std::vector<TileDesc> tiles = make_tiles(cfgs, n);
+    L.ntiles = (int)tiles.size();
+    L.d_tiles = (TileDesc*)cv.take(sizeof(TileDesc) * tiles.size());
+    size_t need_stage = 0;
+    for (int k = 0; k < n; ++k) {
+        const lbm_config& c = cfgs[k];
+        InstDev& I = L.inst[k];
+        I.nx = c.nx;
+        I.ny = c.ny;
+        I.nz = c.nz;
+        I.top_bc = c.top_bc;
+        I.N = (long long)c.nx * c.ny * c.nz;
+        const size_t eb = elem_bytes(c.prec), cb = comp_bytes(c.prec);
+        for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb);
+        for (int p = 0; p < 3; ++p) I.rho[p] = cv.take(2 * I.N * cb);
+        I.cot = (double*)cv.take(sizeof(double) * c.nx * c.ny);
+        I.acc = (double*)cv.take(sizeof(double) * 8);
+        I.err = (int*)cv.take(sizeof(int));
+        I.desc = (double*)cv.take(sizeof(double) * 8);
+        I.t8x = (c.nx + 7) / 8;
+        I.t8y = (c.ny + 7) / 8;
+        I.t8z = (c.nz + 7) / 8;
+        I.nb_max = c.max_beads;
+        I.max_nbr = MAX_NBR;
+        if (c.max_beads > 0) {
+            I.fext = cv.take(3 * I.N * cb);
+            I.ust = cv.take(3 * I.N * cb);
+            I.gcol = cv.take(3 * I.N * cb);
+            I.tflag = (unsigned char*)cv.take((size_t)I.t8x * I.t8y * I.t8z);
+            const size_t vb = sizeof(double) * 3 * c.max_beads;
+            I.bx = (double*)cv.take(vb);
+            I.bv = (double*)cv.take(vb);
+            I.bF = (double*)cv.take(vb);
+            I.bvh = (double*)cv.take(vb);
+            I.bx2 = (double*)cv.take(vb);
+            I.bx0 = (double*)cv.take(vb);
+            I.bfil = (int*)cv.take(sizeof(int) * c.max_beads);
+            I.bpos = (int*)cv.take(sizeof(int) * c.max_beads);
+            I.nbr = (int*)cv.take(sizeof(int) * (size_t)c.max_beads * MAX_NBR);
+            I.nnbr = (int*)cv.take(sizeof(int) * c.max_beads);
+            I.lab = (int*)cv.take(sizeof(int) * 3 * (size_t)c.max_beads);
+            I.max_edges = 8 * c.max_beads + 64;
+            I.edges = (int2*)cv.take(sizeof(int2) * (size_t)I.max_edges);
+            I.nedges = (int*)cv.take(sizeof(int));
+        }
+        need_stage = std::max(need_stage, (size_t)(2 * 19 * I.N * sizeof(double)));
+        need_stage = std::max(need_stage, (size_t)(5 * I.N * sizeof(double)));
+    }
+    L.stage_bytes = std::min(need_stage, STAGE_BYTES);
+    L.stage = (double*)cv.take(L.stage_bytes);
+}
+
+lbm_status check_config(const lbm_config& c) {
+    if (c.nx < 1 || c.ny < 1 || c.nz < 2) return LBM_EINVAL;
+    if ((long long)c.nx * c.ny * c.nz > (1LL << 31)) return LBM_EINVAL;
+    if (c.prec < LBM_FP64 || c.prec > LBM_BF16_SHIFTED) return LBM_EINVAL;
+    if (!(c.tau_R > 0.5) || !(c.tau_B > 0.5)) return LBM_EINVAL;
+    if (!(c.rho0 > 0.0) || c.beta < 0.0 || c.beta > 1.0 || c.sigma < 0.0) return LBM_EINVAL;
+    if (c.J0 < 0.0 || c.K <= 0.0) return LBM_EINVAL;
+    if (c.top_bc != 0 && c.top_bc != 1) return LBM_EINVAL;
+    if (c.shape != 0 && c.shape != 1) return LBM_EINVAL;
+    if (!(c.a > 0 && c.b > 0 && c.c > 0 && c.width > 0)) return LBM_EINVAL;
+    if (!(c.theta_deg > 0.0 && c.theta_deg < 180.0)) return LBM_EINVAL;
+    if (c.max_beads < 0) return LBM_EINVAL;
+    if (c.max_beads > 0) {
+        if (c.substeps < 1 || !(c.bead_mass > 0) || !(c.d0 > 0) || !(c.Rm > c.d0)) return LBM_EINVAL;
+        if (c.rc <= c.d0 && (c.eps_coh > 0 || c.eps_s > 0)) return LBM_EINVAL;
+    }
+    return LBM_OK;
+}
+
+double cot_deg(double t) {
+    const double r = t * (M_PI / 180.0);
+    return cos(r) / sin(r);
+}
+
+}  // namespace
+
+struct lbm_handle {
+    std::vector<lbm_config> cfg;
+    Layout L;
+    cudaStream_t stream = nullptr;
+    long long step = 0;  // host mirror of the device step counter
+    int prec = 0;
+    bool any_beads_cap = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
+    int max_nb = 0;
+};
+
+#define CK(x)                                   \
+    do {                                        \
+        if ((x) != cudaSuccess) {               \
+            (void)cudaGetLastError();           \
+            return LBM_ECUDA;                   \
+        }                                       \
+    } while (0)
+
+namespace {
+
+template <class S>
+lbm_status launch_fused(lbm_handle* h) {
+    k_stream_collide<S, TILE_X, TILE_Y><<<h->L.ntiles, TILE_X * TILE_Y, 0, h->stream>>>(
+        h->L.d_inst, h->L.d_tiles, h->L.glob);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+template <class S>
+lbm_status launch_beads(lbm_handle* h) {
+    using T = typename S::T;
+    const int n = (int)h->cfg.size();
+    if (h->max_nb == 0) return LBM_OK;
+    // clear all coupling-tile flags (contiguous per instance; one memset each)
+    for (int k = 0; k < n; ++k) {
+        const InstDev& I = h->L.inst[k];
+        if (I.tflag) CK(cudaMemsetAsync(I.tflag, 0, (size_t)I.t8x * I.t8y * I.t8z, h->stream));
+    }
+    const int bt = 128;
+    const dim3 gb((h->max_nb + bt - 1) / bt, n);
+    k_bead_begin<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
+    int maxt = 0;
+    for (auto& I : h->L.inst) maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
+    k_bead_field<S><<<dim3(maxt, n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
+    k_bead_nlist<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
+    k_bead_kickdrift<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
+    const int S_ = h->cfg[0].substeps;
+    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<gb, bt, 0, h->stream>>>(h->L.d_inst, s);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+template <class S>
+lbm_status enqueue_step(lbm_handle* h) {
+    lbm_status st = launch_beads<S>(h);
+    if (st != LBM_OK) return st;
+    return launch_fused<S>(h);
+}
+
+lbm_status enqueue_step_any(lbm_handle* h) {
+    switch (h->prec) {
+        case LBM_FP64: return enqueue_step<StoreF64>(h);
+        case LBM_FP32: return enqueue_step<StoreF32>(h);
+        case LBM_FP16_SHIFTED: return enqueue_step<StoreF16>(h);
+        default: return enqueue_step<StoreB16>(h);
+    }
+}
+
+template <class S>
+lbm_status run_moments(lbm_handle* h, int k) {
+    const InstDev& I = h->L.inst[k];
+    const int bt = 256;
+    k_moments<S><<<(unsigned)((I.N + bt - 1) / bt), bt, 0, h->stream>>>(I, h->step, 0, I.N, nullptr);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status run_moments_any(lbm_handle* h, int k) {
+    switch (h->prec) {
+        case LBM_FP64: return run_moments<StoreF64>(h, k);
+        case LBM_FP32: return run_moments<StoreF32>(h, k);
+        case LBM_FP16_SHIFTED: return run_moments<StoreF16>(h, k);
+        default: return run_moments<StoreB16>(h, k);
+    }
+}
+
+lbm_status upload_tables(lbm_handle* h) {
+    CK(cudaMemcpyAsync(h->L.d_inst, h->L.inst.data(), sizeof(InstDev) * h->L.inst.size(),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->graph_dirty = true;
+    return LBM_OK;
+}
+
+lbm_status latched(lbm_handle* h) {
+    int worst = 0;
+    for (auto& I : h->L.inst) {
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, I.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        worst |= e;
+    }
+    if (worst & ERR_NAN) return LBM_ENAN;
+    if (worst & ERR_FENE) return LBM_EFENE;
+    if (worst & ERR_BEAD) return LBM_EBEAD_OOB;
+    if (worst & ERR_TIMEOUT) return LBM_ETIMEOUT;
+    if (worst & ERR_CAP) return LBM_ECAPACITY;
+    return LBM_OK;
+}
+
+template <class S>
+lbm_status init_instance(lbm_handle* h, int k) {
+    const lbm_config& c = h->cfg[k];
+    const InstDev& I = h->L.inst[k];
+    const int bt = 256;
+    k_init_droplet<S><<<(unsigned)((I.N + bt - 1) / bt), bt, 0, h->stream>>>(I, c.shape, c.cx, c.cy, c.cz, c.a,
+                                                                              c.b, c.c, c.width);
+    CK(cudaGetLastError());
+    return run_moments<S>(h, k);
+}
+
+lbm_status init_any(lbm_handle* h, int k) {
+    switch (h->prec) {
+        case LBM_FP64: return init_instance<StoreF64>(h, k);
+        case LBM_FP32: return init_instance<StoreF32>(h, k);
+        case LBM_FP16_SHIFTED: return init_instance<StoreF16>(h, k);
+        default: return init_instance<StoreB16>(h, k);
+    }
+}
+
+
+// populations <-> host FP64 [2][19][N], chunked through the staging buffer
+template <class S>
+lbm_status pop_transfer(lbm_handle* h, int k, double* host, bool to_host) {
+    const InstDev& I = h->L.inst[k];
+    const long long total = 19 * I.N;
+    const long long chunk = (long long)(h->L.stage_bytes / (2 * sizeof(double)));
+    const int bt = 256;
+    for (long long t0 = 0; t0 < total; t0 += chunk) {
+        const long long len = std::min(chunk, total - t0);
+        const unsigned nb = (unsigned)((len + bt - 1) / bt);
+        if (to_host) {
+            k_pop_to_f64<S><<<nb, bt, 0, h->stream>>>(I, h->step, t0, len, h->L.stage);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(host + t0, h->L.stage, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaMemcpyAsync(host + total + t0, h->L.stage + len, len * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+        } else {
+            CK(cudaMemcpyAsync(h->L.stage, host + t0, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(h->L.stage + len, host + total + t0, len * sizeof(double),
+                               cudaMemcpyHostToDevice, h->stream));
+            k_pop_from_f64<S><<<nb, bt, 0, h->stream>>>(I, h->step, t0, len, h->L.stage);
+            CK(cudaGetLastError());
+        }
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+// node fields (moments / colour / fext) -> host FP64, chunked
+template <class S>
+lbm_status node_field(lbm_handle* h, int k, unsigned field, double* host) {
+    using T = typename S::T;
+    const InstDev& I = h->L.inst[k];
+    const int per = field == LBM_FIELD_MOMENTS ? 5 : (field == LBM_FIELD_FEXT ? 3 : 1);
+    const long long chunk = (long long)(h->L.stage_bytes / (per * sizeof(double)));
+    const int bt = 256;
+    for (long long n0 = 0; n0 < I.N; n0 += chunk) {
+        const long long len = std::min(chunk, I.N - n0);
+        const unsigned nb = (unsigned)((per * len + bt - 1) / bt);
+        if (field == LBM_FIELD_MOMENTS)
+            k_moments<S><<<nb, bt, 0, h->stream>>>(I, h->step, n0, len, h->L.stage);
+        else if (field == LBM_FIELD_COLOUR)
+            k_colour<T><<<nb, bt, 0, h->stream>>>(I, h->step, n0, len, h->L.stage);
+        else
+            k_fext<T><<<nb, bt, 0, h->stream>>>(I, n0, len, h->L.stage);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(host + per * n0, h->L.stage, per * len * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+template <class S>
+lbm_status mass_of(lbm_handle* h, int k, double* out2) {
+    const InstDev& I = h->L.inst[k];
+    CK(cudaMemsetAsync(h->L.stage, 0, 2 * sizeof(double), h->stream));
+    k_mass<S><<<4 * 148, 256, 0, h->stream>>>(I, h->step, h->L.stage);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out2, h->L.stage, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+#define DISPATCH(fn, ...)                                          \
+    switch (h->prec) {                                             \
+        case LBM_FP64: return fn<StoreF64>(__VA_ARGS__);           \
+        case LBM_FP32: return fn<StoreF32>(__VA_ARGS__);           \
+        case LBM_FP16_SHIFTED: return fn<StoreF16>(__VA_ARGS__);   \
+        default: return fn<StoreB16>(__VA_ARGS__);                 \
+    }
+
+lbm_status pop_transfer_any(lbm_handle* h, int k, double* host, bool to_host) {
+    DISPATCH(pop_transfer, h, k, host, to_host)
+}
+lbm_status node_field_any(lbm_handle* h, int k, unsigned f, double* host) { DISPATCH(node_field, h, k, f, host) }
+lbm_status mass_any(lbm_handle* h, int k, double* out2) { DISPATCH(mass_of, h, k, out2) }
+
+lbm_status h0_any(lbm_handle* h, int k) {
+    const InstDev& I = h->L.inst[k];
+    CK(cudaMemsetAsync(I.acc + 1, 0, sizeof(double), h->stream));
+    const int ncol = I.nx * I.ny, bt = 256;
+    if (h->prec == LBM_FP64)
+        k_h0<double><<<(ncol + bt - 1) / bt, bt, 0, h->stream>>>(I, h->step);
+    else
+        k_h0<float><<<(ncol + bt - 1) / bt, bt, 0, h->stream>>>(I, h->step);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// capture one time step into a graph (all step dependence lives on the device)
+lbm_status build_graph(lbm_handle* h) {
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    if (h->graph) {
+        cudaGraphDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = h->stream;
+    h->stream = cap;
+    lbm_status st = LBM_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = LBM_ECUDA;
+    if (st == LBM_OK) st = enqueue_step_any(h);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cap, &g) != cudaSuccess) st = LBM_ECUDA;
+    h->stream = saved;
+    cudaStreamDestroy(cap);
+    if (st != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return st;
+    }
+    h->graph = g;
+    CK(cudaGraphInstantiate(&h->gexec, g, 0));
+    h->graph_dirty = false;
+    return LBM_OK;
+}
+
+bool valid_inst(lbm_handle* h, int inst) { return h && inst >= 0 && inst < (int)h->cfg.size(); }
+
+// random straight filaments inside the liquid (C > 0.9), non-overlapping
+lbm_status place_random(lbm_handle* h, int k, int nw, int nbf, double spacing, uint64_t seed,
+                        std::vector<double>& X) {
+    const lbm_config& c = h->cfg[k];
+    const InstDev& I = h->L.inst[k];
+    std::vector<double> C(I.N);
+    lbm_status st = node_field_any(h, k, LBM_FIELD_COLOUR, C.data());
+    if (st != LBM_OK) return st;
+    std::vector<double> have(3 * (size_t)I.nb);
+    if (I.nb) {
+        CK(cudaMemcpy(have.data(), I.bx, sizeof(double) * 3 * I.nb, cudaMemcpyDeviceToHost));
+    }
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    std::normal_distribution<double> G(0.0, 1.0);
+    // bounding box of the liquid
+    int lo[3] = {c.nx, c.ny, c.nz}, hi[3] = {-1, -1, -1};
+    for (long long n = 0; n < I.N; ++n)
+        if (C[n] > 0.9) {
+            const int p[3] = {(int)(n % c.nx), (int)((n / c.nx) % c.ny), (int)(n / ((long long)c.nx * c.ny))};
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], p[d]);
+                hi[d] = std::max(hi[d], p[d]);
+            }
+        }
+    if (hi[0] < 0) return LBM_EINVAL;
+    auto colour_at = [&](const double* P) {
+        // nearest-node colour (placement only needs "well inside the liquid")
+        const int x = wrapi((int)lround(P[0]), c.nx), y = wrapi((int)lround(P[1]), c.ny);
+        const int z = (int)lround(P[2]);
+        if (z < 0 || z >= c.nz) return -1.0;
+        return C[((long long)z * c.ny + y) * c.nx + x];
+    };
+    std::vector<double> placed = have;
+    const long long max_tries = 200000LL + 2000LL * nw;
+    long long tries = 0;
+    int got = 0;
+    while (got < nw && tries < max_tries) {
+        ++tries;
+        double cen[3], dir[3];
+        for (int d = 0; d < 3; ++d) cen[d] = lo[d] + U(rng) * (hi[d] - lo[d] + 1);
+        double nrm = 0;
+        for (int d = 0; d < 3; ++d) {
+            dir[d] = G(rng);
+            nrm += dir[d] * dir[d];
+        }
+        nrm = sqrt(nrm);
+        if (nrm == 0) continue;
+        for (int d = 0; d < 3; ++d) dir[d] /= nrm;
+        std::vector<double> cand(3 * nbf);
+        bool ok = true;
+        for (int b = 0; b < nbf && ok; ++b) {
+            for (int d = 0; d < 3; ++d) cand[3 * b + d] = cen[d] + (b - (nbf - 1) / 2.0) * spacing * dir[d];
+            if (cand[3 * b + 2] < 1.0 || cand[3 * b + 2] > c.nz - 2.0) ok = false;
+            if (ok && colour_at(&cand[3 * b]) <= 0.9) ok = false;
+        }
+        for (size_t q = 0; q < placed.size() / 3 && ok; ++q)
+            for (int b = 0; b < nbf && ok; ++b) {
+                double dd = 0;
+                for (int d = 0; d < 3; ++d) {
+                    double e = cand[3 * b + d] - placed[3 * q + d];
+                    if (d == 0) e -= c.nx * floor(e / c.nx + 0.5);
+                    if (d == 1) e -= c.ny * floor(e / c.ny + 0.5);
+                    dd += e * e;
+                }
+                if (dd <= c.d0 * c.d0) ok = false;
+            }
+        if (!ok) continue;
+        for (int b = 0; b < nbf; ++b) {
+            cand[3 * b] -= c.nx * floor(cand[3 * b] / c.nx);
+            cand[3 * b + 1] -= c.ny * floor(cand[3 * b + 1] / c.ny);
+        }
+        placed.insert(placed.end(), cand.begin(), cand.end());
+        X.insert(X.end(), cand.begin(), cand.end());
+        ++got;
+    }
+    return got == nw ? LBM_OK : LBM_EINVAL;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public C ABI
+// ===========================================================================
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_config* cfgs, int n) {
+    if (!cfgs || n < 1) return 0;
+    Carver cv{nullptr};
+    Layout L;
+    carve(cfgs, n, cv, L);
+    return align_up(cv.off, 256);
+}
+
+lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_bytes, void* stream,
+                      lbm_handle** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (!cfgs || n < 1 || !dev_ws) return LBM_EINVAL;
+    if (((uintptr_t)dev_ws) & 15) return LBM_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        lbm_status st = check_config(cfgs[k]);
+        if (st != LBM_OK) return st;
+        if (cfgs[k].prec != cfgs[0].prec) return LBM_EINVAL;
+        if (cfgs[k].max_beads > 0 && cfgs[0].max_beads > 0 && cfgs[k].substeps != cfgs[0].substeps)
+            return LBM_EINVAL;
+    }
+    if (ws_bytes < lbm_workspace_bytes(cfgs, n)) return LBM_ENOMEM_WS;
+    lbm_handle* h = new lbm_handle();
+    h->cfg.assign(cfgs, cfgs + n);
+    h->stream = (cudaStream_t)stream;
+    h->prec = cfgs[0].prec;
+    Carver cv{(char*)dev_ws};
+    carve(cfgs, n, cv, h->L);
+    // substeps must match across instances with beads: use the first with beads
+    for (int k = 0; k < n; ++k)
+        if (cfgs[k].max_beads > 0) {
+            for (auto& c : h->cfg) c.substeps = cfgs[k].substeps;
+            break;
+        }
+    lbm_status st = LBM_OK;
+    auto fail = [&](lbm_status s) {
+        delete h;
+        return s;
+    };
+    if (cudaMemsetAsync(h->L.glob, 0, sizeof(StepGlobals), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    std::vector<TileDesc> tiles = make_tiles(cfgs, n);
+    if (cudaMemcpyAsync(h->L.d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+        return fail(LBM_ECUDA);
+    for (int k = 0; k < n; ++k) {
+        const lbm_config& c = h->cfg[k];
+        InstDev& I = h->L.inst[k];
+        I.tau_R = c.tau_R;
+        I.tau_B = c.tau_B;
+        I.beta = c.beta;
+        I.sigma = c.sigma;
+        I.rho0 = c.rho0;
+        I.J0 = c.J0;
+        I.K = c.K;
+        for (int d = 0; d < 3; ++d) I.body[d] = c.body[d];
+        I.evap_start = c.evap_start;
+        I.substeps = c.substeps;
+        I.ks = c.ks;
+        I.Rm = c.Rm;
+        I.d0 = c.d0;
+        I.eps_wca = c.eps_wca;
+        I.kb = c.kb;
+        I.eps_coh = c.eps_coh;
+        I.eps_s = c.eps_s;
+        I.rc = c.rc;
+        I.gamma = c.gamma;
+        I.xi = c.xi;
+        I.mu = c.mu;
+        I.gamma_t = c.gamma_t;
+        I.mass = c.bead_mass;
+        double rl = c.d0;
+        if (c.eps_coh > 0) rl = std::max(rl, c.rc);
+        rl = std::max(rl, c.rcon);
+        I.rlist = rl + 1.0;
+        I.rcon = c.rcon;
+        I.x_src = c.x_src;
+        I.x_snk = c.x_snk;
+        I.nb = 0;
+        std::vector<double> cot((size_t)c.nx * c.ny, cot_deg(c.theta_deg));
+        if (cudaMemcpyAsync(I.cot, cot.data(), sizeof(double) * cot.size(), cudaMemcpyHostToDevice, h->stream) !=
+                cudaSuccess ||
+            cudaMemsetAsync(I.acc, 0, sizeof(double) * 8, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(I.err, 0, sizeof(int), h->stream) != cudaSuccess)
+            return fail(LBM_ECUDA);
+        if (I.fext) {
+            const size_t cb = comp_bytes(c.prec);
+            if (cudaMemsetAsync(I.fext, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.ust, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.gcol, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.tflag, 0, (size_t)I.t8x * I.t8y * I.t8z, h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.bF, 0, sizeof(double) * 3 * c.max_beads, h->stream) != cudaSuccess)
+                return fail(LBM_ECUDA);
+        }
+        // cot is needed by cudaMemcpyAsync until the copy ends
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    }
+    st = upload_tables(h);
+    if (st != LBM_OK) return fail(st);
+    for (int k = 0; k < n; ++k) {
+        st = init_any(h, k);
+        if (st != LBM_OK) return fail(st);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(LBM_ECUDA);
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_substrate_pattern(lbm_handle* h, int inst, const double* theta) {
+    if (!valid_inst(h, inst) || !theta) return LBM_EINVAL;
+    const lbm_config& c = h->cfg[inst];
+    std::vector<double> cot((size_t)c.nx * c.ny);
+    for (size_t a = 0; a < cot.size(); ++a) {
+        if (!(theta[a] > 0.0 && theta[a] < 180.0)) return LBM_EINVAL;
+        cot[a] = cot_deg(theta[a]);
+    }
+    CK(cudaMemcpyAsync(h->L.inst[inst].cot, cot.data(), sizeof(double) * cot.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_add_nanowires(lbm_handle* h, int inst, int n_wires, double length, const double* centers,
+                             const double* dirs, uint64_t seed) {
+    if (!valid_inst(h, inst) || n_wires < 0 || !(length > 0)) return LBM_EINVAL;
+    if ((centers == nullptr) != (dirs == nullptr)) return LBM_EINVAL;
+    const lbm_config& c = h->cfg[inst];
+    InstDev& I = h->L.inst[inst];
+    if (c.max_beads == 0) return LBM_ECAPACITY;
+    const int nbf = std::max(1, (int)lround(length / c.d0));
+    if ((long long)I.nb + (long long)n_wires * nbf > c.max_beads) return LBM_ECAPACITY;
+    if (n_wires == 0) return LBM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<double> X;
+    if (centers) {
+        for (int w = 0; w < n_wires; ++w) {
+            double d[3] = {dirs[3 * w], dirs[3 * w + 1], dirs[3 * w + 2]};
+            const double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (!(nn > 0)) return LBM_EINVAL;
+            for (int b = 0; b < nbf; ++b) {
+                double P[3];
+                for (int k = 0; k < 3; ++k) P[k] = centers[3 * w + k] + (b - (nbf - 1) / 2.0) * c.d0 * d[k] / nn;
+                P[0] -= c.nx * floor(P[0] / c.nx);
+                P[1] -= c.ny * floor(P[1] / c.ny);
+                if (!(P[2] > -0.5 && P[2] < c.nz - 0.5)) return LBM_EINVAL;
+                X.insert(X.end(), P, P + 3);
+            }
+        }
+    } else {
+        lbm_status st = place_random(h, inst, n_wires, nbf, c.d0, seed ? seed : c.seed, X);
+        if (st != LBM_OK) return st;
+    }
+    // filament ids continue after the existing ones
+    int fil0 = 0;
+    if (I.nb > 0) {
+        int lastfil = 0;
+        CK(cudaMemcpy(&lastfil, I.bfil + I.nb - 1, sizeof(int), cudaMemcpyDeviceToHost));
+        fil0 = lastfil + 1;
+    }
+    const int nadd = n_wires * nbf;
+    std::vector<int> fil(nadd), pos(nadd);
+    for (int w = 0; w < n_wires; ++w)
+        for (int b = 0; b < nbf; ++b) {
+            fil[w * nbf + b] = fil0 + w;
+            pos[w * nbf + b] = b;
+        }
+    std::vector<double> zero(3 * (size_t)nadd, 0.0);
+    CK(cudaMemcpy(I.bx + 3 * I.nb, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(I.bv + 3 * I.nb, zero.data(), sizeof(double) * zero.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(I.bF + 3 * I.nb, zero.data(), sizeof(double) * zero.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(I.bfil + I.nb, fil.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(I.bpos + I.nb, pos.data(), sizeof(int) * nadd, cudaMemcpyHostToDevice));
+    I.nb += nadd;
+    h->max_nb = 0;
+    for (auto& J : h->L.inst) h->max_nb = std::max(h->max_nb, J.nb);
+    return upload_tables(h);
+}
+
+lbm_status lbm_step(lbm_handle* h, int n_steps) {
+    if (!h || n_steps < 0) return LBM_EINVAL;
+    const int n = (int)h->cfg.size();
+    for (int s = 0; s < n_steps; ++s) {
+        // h0 is taken from the moments of the first evaporating step
+        for (int k = 0; k < n; ++k) {
+            const lbm_config& c = h->cfg[k];
+            if (c.J0 > 0 && c.evap_start >= 0 && h->step == c.evap_start) {
+                lbm_status st = h0_any(h, k);
+                if (st != LBM_OK) return st;
+            }
+        }
+        if (n_steps - s >= 2 || h->gexec) {
+            if (h->graph_dirty) {
+                lbm_status st = build_graph(h);
+                if (st != LBM_OK) return st;
+            }
+            CK(cudaGraphLaunch(h->gexec, h->stream));
+        } else {
+            lbm_status st = enqueue_step_any(h);
+            if (st != LBM_OK) return st;
+        }
+        ++h->step;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, double* ms_step) {
+    if (!h || n_steps < 1 || !ms_fluid || !ms_step) return LBM_EINVAL;
+    const int n = (int)h->cfg.size();
+    std::vector<cudaEvent_t> ev(3 * (size_t)n_steps + 1, nullptr);
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto& f : ev)
+                if (f) cudaEventDestroy(f);
+            return LBM_ECUDA;
+        }
+    lbm_status st = LBM_OK;
+    for (int s = 0; s < n_steps && st == LBM_OK; ++s) {
+        cudaEventRecord(ev[3 * s], h->stream);
+        for (int k = 0; k < n && st == LBM_OK; ++k) {
+            const lbm_config& c = h->cfg[k];
+            if (c.J0 > 0 && c.evap_start >= 0 && h->step == c.evap_start) st = h0_any(h, k);
+        }
+        if (st != LBM_OK) break;
+        switch (h->prec) {
+            case LBM_FP64: st = launch_beads<StoreF64>(h); break;
+            case LBM_FP32: st = launch_beads<StoreF32>(h); break;
+            case LBM_FP16_SHIFTED: st = launch_beads<StoreF16>(h); break;
+            default: st = launch_beads<StoreB16>(h); break;
+        }
+        if (st != LBM_OK) break;
+        cudaEventRecord(ev[3 * s + 1], h->stream);
+        switch (h->prec) {
+            case LBM_FP64: st = launch_fused<StoreF64>(h); break;
+            case LBM_FP32: st = launch_fused<StoreF32>(h); break;
+            case LBM_FP16_SHIFTED: st = launch_fused<StoreF16>(h); break;
+            default: st = launch_fused<StoreB16>(h); break;
+        }
+        cudaEventRecord(ev[3 * s + 2], h->stream);
+        ++h->step;
+    }
+    cudaEventRecord(ev[3 * (size_t)n_steps], h->stream);
+    double tf = 0.0, ts = 0.0;
+    if (st == LBM_OK && cudaStreamSynchronize(h->stream) == cudaSuccess) {
+        for (int s = 0; s < n_steps; ++s) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[3 * s + 1], ev[3 * s + 2]);
+            cudaEventElapsedTime(&b, ev[3 * s], ev[3 * s + 3 <= 3 * n_steps ? 3 * s + 3 : 3 * n_steps]);
+            tf += a;
+            ts += b;
+        }
+        *ms_fluid = tf / n_steps;
+        *ms_step = ts / n_steps;
+    } else if (st == LBM_OK) {
+        st = LBM_ECUDA;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    (void)cudaGetLastError();
+    return st;
+}
+
+lbm_status lbm_sync(lbm_handle* h) {
+    if (!h) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    return latched(h);
+}
+
+lbm_status lbm_clear_error(lbm_handle* h) {
+    if (!h) return LBM_EINVAL;
+    for (auto& I : h->L.inst) CK(cudaMemsetAsync(I.err, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+static size_t field_bytes(const lbm_config& c, int nb, unsigned f) {
+    const size_t N = (size_t)c.nx * c.ny * c.nz;
+    switch (f) {
+        case LBM_FIELD_POPULATIONS: return 2 * 19 * N * 8;
+        case LBM_FIELD_MOMENTS: return 5 * N * 8;
+        case LBM_FIELD_COLOUR: return N * 8;
+        case LBM_FIELD_BEAD_X:
+        case LBM_FIELD_BEAD_V:
+        case LBM_FIELD_BEAD_F: return 3 * (size_t)nb * 8;
+        case LBM_FIELD_BEAD_TOPO: return 2 * (size_t)nb * 4;
+        case LBM_FIELD_ACCUM: return 6 * 8;
+        case LBM_FIELD_FEXT: return 3 * N * 8;
+        case LBM_FIELD_THETA_COT: return (size_t)c.nx * c.ny * 8;
+        default: return 0;
+    }
+}
+
+lbm_status lbm_read_fields(lbm_handle* h, int inst, unsigned field, void* dst, size_t bytes) {
+    if (!valid_inst(h, inst) || !dst) return LBM_EINVAL;
+    const lbm_config& c = h->cfg[inst];
+    const InstDev& I = h->L.inst[inst];
+    const size_t need = field_bytes(c, I.nb, field);
+    if (need == 0 || bytes != need) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    lbm_status st = LBM_OK;
+    switch (field) {
+        case LBM_FIELD_POPULATIONS: st = pop_transfer_any(h, inst, (double*)dst, true); break;
+        case LBM_FIELD_MOMENTS:
+        case LBM_FIELD_COLOUR: st = node_field_any(h, inst, field, (double*)dst); break;
+        case LBM_FIELD_FEXT:
+            if (!I.fext) {
+                memset(dst, 0, bytes);
+                break;
+            }
+            st = node_field_any(h, inst, field, (double*)dst);
+            break;
+        case LBM_FIELD_BEAD_X:
+        case LBM_FIELD_BEAD_V:
+        case LBM_FIELD_BEAD_F: {
+            if (I.nb == 0) break;
+            const double* p = field == LBM_FIELD_BEAD_X ? I.bx : (field == LBM_FIELD_BEAD_V ? I.bv : I.bF);
+            CK(cudaMemcpy(dst, p, bytes, cudaMemcpyDeviceToHost));
+            break;
+        }
+        case LBM_FIELD_BEAD_TOPO: {
+            if (I.nb == 0) break;
+            std::vector<int> f(I.nb), p(I.nb);
+            CK(cudaMemcpy(f.data(), I.bfil, sizeof(int) * I.nb, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(p.data(), I.bpos, sizeof(int) * I.nb, cudaMemcpyDeviceToHost));
+            int* o = (int*)dst;
+            for (int a = 0; a < I.nb; ++a) {
+                o[2 * a] = f[a];
+                o[2 * a + 1] = p[a];
+            }
+            break;
+        }
+        case LBM_FIELD_ACCUM: {
+            double a[8];
+            CK(cudaMemcpy(a, I.acc, sizeof(a), cudaMemcpyDeviceToHost));
+            double* o = (double*)dst;
+            o[0] = (double)h->step;
+            o[1] = a[1];
+            o[2] = a[2];
+            o[3] = a[3];
+            o[4] = a[4];
+            o[5] = (double)I.nb;
+            break;
+        }
+        case LBM_FIELD_THETA_COT: CK(cudaMemcpy(dst, I.cot, bytes, cudaMemcpyDeviceToHost)); break;
+    }
+    if (st != LBM_OK) return st;
+    return latched(h);
+}
+
+lbm_status lbm_write_fields(lbm_handle* h, int inst, unsigned field, const void* src, size_t bytes) {
+    if (!valid_inst(h, inst) || !src) return LBM_EINVAL;
+    const lbm_config& c = h->cfg[inst];
+    InstDev& I = h->L.inst[inst];
+    const size_t need = field_bytes(c, I.nb, field);
+    if (need == 0 || bytes != need) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    switch (field) {
+        case LBM_FIELD_POPULATIONS: {
+            lbm_status st = pop_transfer_any(h, inst, (double*)src, false);
+            if (st != LBM_OK) return st;
+            st = run_moments_any(h, inst);
+            if (st != LBM_OK) return st;
+            CK(cudaStreamSynchronize(h->stream));
+            return LBM_OK;
+        }
+        case LBM_FIELD_BEAD_X:
+        case LBM_FIELD_BEAD_V:
+        case LBM_FIELD_BEAD_F: {
+            if (I.nb == 0) return LBM_OK;
+            double* p = field == LBM_FIELD_BEAD_X ? I.bx : (field == LBM_FIELD_BEAD_V ? I.bv : I.bF);
+            CK(cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice));
+            return LBM_OK;
+        }
+        case LBM_FIELD_ACCUM: {
+            const double* a = (const double*)src;
+            if (a[0] < 0 || a[0] != floor(a[0])) return LBM_EINVAL;
+            // the step counter is shared by all instances of the handle
+            h->step = (long long)a[0];
+            StepGlobals g{h->step, 0u, 0};
+            CK(cudaMemcpy(h->L.glob, &g, sizeof(g), cudaMemcpyHostToDevice));
+            double v[8] = {a[0], a[1], a[2], a[3], a[4], 0, 0, 0};
+            CK(cudaMemcpy(I.acc, v, sizeof(v), cudaMemcpyHostToDevice));
+            return LBM_OK;
+        }
+        default: return LBM_EINVAL;
+    }
+}
+
+lbm_status lbm_deposit_descriptors(lbm_handle* h, int inst, lbm_descriptors* out) {
+    if (!valid_inst(h, inst) || !out) return LBM_EINVAL;
+    const InstDev& I = h->L.inst[inst];
+    memset(out, 0, sizeof(*out));
+    CK(cudaStreamSynchronize(h->stream));
+    if (I.nb > 0) {
+        CK(cudaMemsetAsync(I.nedges, 0, sizeof(int), h->stream));
+        k_desc_edges<<<(I.nb + 127) / 128, 128, 0, h->stream>>>(h->L.d_inst, inst);
+        k_desc_solve<<<1, 1024, 0, h->stream>>>(h->L.d_inst, inst);
+        CK(cudaGetLastError());
+        double d[8];
+        CK(cudaMemcpyAsync(d, I.desc, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        out->S_x = d[0];
+        out->n_clusters = (int)d[1];
+        out->percolates = (int)d[2];
+        out->n_bonds = (int)d[3];
+    }
+    out->n_beads = I.nb;
+    double m[2];
+    lbm_status st = mass_any(h, inst, m);
+    if (st != LBM_OK) return st;
+    out->mass_R = m[0];
+    out->mass_B = m[1];
+    double a[8];
+    CK(cudaMemcpy(a, I.acc, sizeof(a), cudaMemcpyDeviceToHost));
+    out->h0 = a[1];
+    out->evaporated = a[2];
+    out->top_in = a[3];
+    out->top_out = a[4];
+    out->step = h->step;
+    return latched(h);
+}
+
+lbm_status lbm_destroy(lbm_handle* h) {
+    if (!h) return LBM_EINVAL;
+    cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    delete h;
+    return LBM_OK;
+}
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument or configuration";
+        case LBM_ENOMEM_WS: return "workspace too small";
+        case LBM_ECUDA: return "CUDA runtime error";
+        case LBM_ENAN: return "non-finite or non-positive density";
+        case LBM_EFENE: return "FENE bond reached its maximum extension";
+        case LBM_EBEAD_OOB: return "bead left the fluid or moved too far in one step";
+        case LBM_ETIMEOUT: return "device-side wait gave up";
+        case LBM_ESTATE: return "call not valid in the current state";
+        case LBM_ECAPACITY: return "capacity exceeded";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

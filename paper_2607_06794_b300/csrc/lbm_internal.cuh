@@ -1,0 +1,222 @@
+// Internal device-side definitions of the B300 library: lattice constants,
+// population storage formats, per-instance tables.  Paper references are to
+// "Evaporation-Driven Nanowire Self-Assembly in an Elongated Droplet", Sec. II.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity set (Sec. II.A, Eq. (1)): rest, 6 axis links, 12 face
+// diagonals.  Directions come in opposite pairs (2k-1, 2k).  Written as
+// constexpr functions so that fully unrolled loops fold every c_i and w_i.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double wq(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+// 1/|c_i| for the recolouring direction cosine
+__host__ __device__ constexpr double inv_len(int i) {
+    return i == 0 ? 0.0 : (i <= 6 ? 1.0 : 0.70710678118654752440);
+}
+
+// error bits latched per instance
+enum : int { ERR_NAN = 1, ERR_FENE = 2, ERR_BEAD = 4, ERR_TIMEOUT = 8, ERR_CAP = 16 };
+
+// ---------------------------------------------------------------------------
+// Population storage.  Layout per buffer: [comp][dir][z][y][x], comp stride
+// 19*N, dir stride N.  load() returns (f^R, f^B) in the compute type; store()
+// writes a post-collision pair and returns the values as they will be read
+// back (quantised), so moments pushed from them match the next pull exactly.
+// ---------------------------------------------------------------------------
+struct StoreF64 {
+    using T = double;
+    using E = double;
+    static __device__ __forceinline__ void load(const E* __restrict__ p, long long cs, long long k,
+                                                T w, T rho0, T& r, T& b) {
+        r = __ldg(p + k);
+        b = __ldg(p + cs + k);
+    }
+    static __device__ __forceinline__ void store(E* __restrict__ p, long long cs, long long k, T w,
+                                                 T rho0, T r, T b, T& rq, T& bq) {
+        p[k] = r;
+        p[cs + k] = b;
+        rq = r;
+        bq = b;
+    }
+    static __host__ __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
+                                           double& r, double& b) {
+        r = p[k];
+        b = p[cs + k];
+    }
+    static __host__ __device__ void from_f64(E* p, long long cs, long long k, int i, double rho0,
+                                             double r, double b) {
+        p[k] = r;
+        p[cs + k] = b;
+    }
+};
+
+struct StoreF32 {
+    using T = float;
+    using E = float;
+    static __device__ __forceinline__ void load(const E* __restrict__ p, long long cs, long long k,
+                                                T w, T rho0, T& r, T& b) {
+        r = __ldg(p + k);
+        b = __ldg(p + cs + k);
+    }
+    static __device__ __forceinline__ void store(E* __restrict__ p, long long cs, long long k, T w,
+                                                 T rho0, T r, T b, T& rq, T& bq) {
+        p[k] = r;
+        p[cs + k] = b;
+        rq = r;
+        bq = b;
+    }
+    static __host__ __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
+                                           double& r, double& b) {
+        r = p[k];
+        b = p[cs + k];
+    }
+    static __host__ __device__ void from_f64(E* p, long long cs, long long k, int i, double rho0,
+                                             double r, double b) {
+        p[k] = (float)r;
+        p[cs + k] = (float)b;
+    }
+};
+
+// Shifted 16-bit storage: comp 0 holds F_i - w_i rho0 (total population as a
+// deviation from rest), comp 1 holds f^R_i/F_i - 1/2 (liquid fraction; exactly
+// +-1/2 in pure phases).  H is __half or __nv_bfloat16.
+template <class H>
+struct Cvt;
+template <>
+struct Cvt<__half> {
+    static __device__ __forceinline__ float f(__half h) { return __half2float(h); }
+    static __device__ __forceinline__ __half h(float f) { return __float2half_rn(f); }
+    static __host__ __device__ float fh(__half h) { return __half2float(h); }
+    static __host__ __device__ __half hf(float f) { return __float2half_rn(f); }
+};
+template <>
+struct Cvt<__nv_bfloat16> {
+    static __device__ __forceinline__ float f(__nv_bfloat16 h) { return __bfloat162float(h); }
+    static __device__ __forceinline__ __nv_bfloat16 h(float f) { return __float2bfloat16_rn(f); }
+    static __host__ __device__ float fh(__nv_bfloat16 h) { return __bfloat162float(h); }
+    static __host__ __device__ __nv_bfloat16 hf(float f) { return __float2bfloat16_rn(f); }
+};
+
+template <class H>
+struct StoreShift16 {
+    using T = float;
+    using E = H;
+    static __host__ __device__ __forceinline__ void decode(float P, float psi, float w, float rho0,
+                                                           float& r, float& b) {
+        float F = P + w * rho0;
+        r = (psi + 0.5f) * F;
+        b = F - r;
+    }
+    static __device__ __forceinline__ void load(const E* __restrict__ p, long long cs, long long k,
+                                                T w, T rho0, T& r, T& b) {
+        float P = Cvt<H>::f(p[k]);
+        float psi = Cvt<H>::f(p[cs + k]);
+        decode(P, psi, w, rho0, r, b);
+    }
+    static __device__ __forceinline__ void store(E* __restrict__ p, long long cs, long long k, T w,
+                                                 T rho0, T r, T b, T& rq, T& bq) {
+        float F = r + b;
+        H qP = Cvt<H>::h(F - w * rho0);
+        H qs = Cvt<H>::h(F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f);
+        p[k] = qP;
+        p[cs + k] = qs;
+        decode(Cvt<H>::f(qP), Cvt<H>::f(qs), w, rho0, rq, bq);
+    }
+    static __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
+                                  double& r, double& b) {
+        float rr, bb;
+        decode(Cvt<H>::f(p[k]), Cvt<H>::f(p[cs + k]), (float)wq(i), (float)rho0, rr, bb);
+        r = rr;
+        b = bb;
+    }
+    static __device__ void from_f64(E* p, long long cs, long long k, int i, double rho0, double r,
+                                    double b) {
+        float F = (float)(r + b);
+        p[k] = Cvt<H>::h(F - (float)wq(i) * (float)rho0);
+        p[cs + k] = Cvt<H>::h(F != 0.0f ? (float)(r / (r + b)) - 0.5f : 0.0f);
+    }
+};
+using StoreF16 = StoreShift16<__half>;
+using StoreB16 = StoreShift16<__nv_bfloat16>;
+
+// ---------------------------------------------------------------------------
+// Device tables
+// ---------------------------------------------------------------------------
+struct InstDev {
+    int nx, ny, nz, top_bc;
+    long long N;
+    int t8x, t8y, t8z;           // 8^3 coupling-tile grid
+    int pad0;
+    void* pop[2];                // population buffers (storage type)
+    void* rho[3];                // moment buffers: [2][N] rho_R, rho_B (compute type)
+    void* fext;                  // [N][3] bead force on the fluid (compute type)
+    void* ust;                   // [N][3] u* near beads (compute type)
+    void* gcol;                  // [N][3] grad C near beads (compute type)
+    unsigned char* tflag;        // [t8z][t8y][t8x] coupling-tile flags
+    double* cot;                 // [ny][nx] cot(theta)
+    double* acc;                 // [8]: step, h0, evaporated, top_in, top_out, ...
+    int* err;                    // latched error bits
+    double tau_R, tau_B, beta, sigma, rho0, J0, K;
+    double body[3];
+    long long evap_start;
+    // filaments
+    int nb, nb_max, substeps, max_nbr;
+    double* bx;
+    double* bv;
+    double* bF;
+    double* bvh;
+    double* bx2;
+    double* bx0;
+    int* bfil;
+    int* bpos;
+    int* nbr;
+    int* nnbr;
+    double ks, Rm, d0, eps_wca, kb, eps_coh, eps_s, rc, gamma, xi, mu, gamma_t, mass, rlist;
+    // descriptors
+    double rcon, x_src, x_snk;
+    int* lab;
+    int2* edges;
+    int* nedges;
+    int max_edges;
+    int pad1;
+    double* desc;                // [8] descriptor results
+};
+
+struct StepGlobals {
+    long long step;
+    unsigned int done;
+    int pad;
+};
+
+struct TileDesc {
+    int inst, x0, y0, z0, z1, pad0, pad1, pad2;
+};
+
+__host__ __device__ inline int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+}  // namespace lbm

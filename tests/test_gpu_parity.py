@@ -1,0 +1,232 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (per population, relative to |f| + w_i):
+  FP64 storage+arithmetic: 1e-12 per step (only the summation order differs)
+  FP32: 2e-6 (single-precision rounding of a few dozen operations on O(0.3) values)
+  FP16 shifted: 2e-3 (stored liquid fraction carries 2^-11 relative error, total 2^-11)
+  BF16 shifted: 1.5e-2 (8-bit significands: 2^-8 relative)
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from tests import inputs
+from tests.gpu_helpers import W, oracle_params, oracle_state, pop_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-6, "fp16": 2e-3, "bf16": 1.5e-2}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2607_06794_b300 import build
+    build.build()
+    import paper_2607_06794_b300 as P
+    return P
+
+
+def droplet_cfg(P, nx=40, ny=24, nz=20, **kw):
+    base = dict(cx=nx / 2 - 0.5, cy=ny / 2 - 0.5, cz=-0.5, a=nx * 0.3, b=ny * 0.3, c=nz * 0.55,
+                sigma=0.01, beta=0.7, top_bc=1, theta_deg=70.0)
+    base.update(kw)
+    return P.Config(nx, ny, nz, **base)
+
+
+def run_pair(P, oracle, cfg, warm=15, steps=1, theta=None, beads=None):
+    p, fR, fB, cot = oracle_state(oracle, cfg, warm, theta)
+    sim = P.Simulation([cfg])
+    if theta is not None:
+        sim.set_substrate_pattern(0, theta)
+    sim.write(0, "populations", np.stack([fR, fB]))
+    ob = None
+    if beads is not None:
+        fil, pos, X = beads
+        n_b = int(np.max(pos)) + 1
+        nw = len(X) // n_b
+        cen = X.reshape(nw, n_b, 3).mean(axis=1)
+        dirs = X.reshape(nw, n_b, 3)[:, -1] - X.reshape(nw, n_b, 3)[:, 0]
+        sim.add_nanowires(0, nw, n_b * cfg.d0, cen, dirs)
+        ob = oracle.Beads(fil, pos, sim_free_positions(cen, dirs, n_b, cfg))
+    acc = oracle.Acc()
+    for _ in range(steps):
+        oracle.step(p, fR, fB, cot, acc, ob)
+    sim.step(steps)
+    sim.sync()
+    return sim, p, fR, fB, cot, acc, ob
+
+
+def sim_free_positions(cen, dirs, n_b, cfg):
+    """Bead positions of straight filaments built on the test side (same rule as the library)."""
+    d = dirs / np.linalg.norm(dirs, axis=1, keepdims=True)
+    X = np.concatenate([[c + (k - (n_b - 1) / 2.0) * cfg.d0 * dd for k in range(n_b)] for c, dd in zip(cen, d)])
+    X[:, 0] %= cfg.nx
+    X[:, 1] %= cfg.ny
+    return X
+
+
+# ---------------------------------------------------------------------------- fluid
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_one_step_matches_oracle(lbm, oracle, prec):
+    cfg = droplet_cfg(lbm, prec=prec)
+    theta = inputs.stripe_angles(cfg.nx, cfg.ny, 8, 60.0, 110.0)
+    sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg, theta=theta)
+    got = sim.read(0, "populations")
+    assert pop_err(got, fR, fB) < TOL[prec]
+
+
+def test_fp64_ten_steps_with_evaporation_and_budgets(lbm, oracle):
+    cfg = droplet_cfg(lbm, prec="fp64", J0=2e-3, evap_start=0)
+    sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg, steps=10)
+    got = sim.read(0, "populations")
+    assert pop_err(got, fR, fB) < 1e-11
+    a = sim.read(0, "accum")
+    assert a[0] == 10
+    assert a[1] == pytest.approx(acc.h0, rel=1e-13)
+    assert acc.evaporated > 0
+    assert a[2] == pytest.approx(acc.evaporated, rel=1e-11)
+    assert a[3] == pytest.approx(acc.top_in, rel=1e-12)
+    assert a[4] == pytest.approx(acc.top_out, rel=1e-11)
+
+
+def test_fp64_moments_and_colour_match_oracle_fields(lbm, oracle):
+    cfg = droplet_cfg(lbm, prec="fp64")
+    sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg)
+    f = oracle.fields(p, fR, fB, cot)
+    m = sim.read(0, "moments")
+    assert np.allclose(m[..., 0], f["rhoR"], rtol=1e-13, atol=1e-15)
+    assert np.allclose(m[..., 1], f["rhoB"], rtol=1e-13, atol=1e-15)
+    assert np.allclose(m[..., 2:], f["j"], rtol=1e-11, atol=1e-15)
+    assert np.allclose(sim.read(0, "colour"), f["C"], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [(5, 3, 4), (33, 9, 7), (1, 1, 6), (64, 8, 3)])
+def test_ragged_and_tiny_lattices(lbm, oracle, shape):
+    nx, ny, nz = shape
+    cfg = lbm.Config(nx, ny, nz, prec="fp64", cx=nx / 2, cy=ny / 2, cz=-0.5, a=max(nx * 0.4, 1),
+                     b=max(ny * 0.4, 1), c=nz * 0.6, sigma=0.02, top_bc=1, theta_deg=75.0,
+                     J0=1e-3, evap_start=0, body=(1e-5, 0, 0))
+    sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg, warm=3, steps=3)
+    assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-12
+
+
+def test_top_wall_and_body_force(lbm, oracle):
+    cfg = droplet_cfg(lbm, prec="fp64", top_bc=0, body=(2e-6, -1e-6, 0.0))
+    sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg, steps=4)
+    assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-12
+
+
+def test_gpu_initial_droplet_matches_oracle(lbm, oracle):
+    for prec in ("fp64", "fp32"):
+        cfg = droplet_cfg(lbm, prec=prec)
+        sim = lbm.Simulation([cfg])
+        p = oracle_params(oracle, cfg)
+        fR, fB = oracle.init_droplet(p, 0, cfg.cx, cfg.cy, cfg.cz, cfg.a, cfg.b, cfg.c, cfg.width)
+        assert pop_err(sim.read(0, "populations"), fR, fB) < (1e-14 if prec == "fp64" else 1e-7)
+
+
+def test_fp32_mass_is_conserved_over_many_steps(lbm, oracle):
+    cfg = droplet_cfg(lbm, prec="fp32", top_bc=0)
+    sim = lbm.Simulation([cfg])
+    d0 = sim.descriptors(0)
+    sim.step(300)
+    d1 = sim.descriptors(0)
+    assert abs(d1["mass_R"] - d0["mass_R"]) < 1e-5 * d0["mass_R"]
+    assert abs(d1["mass_B"] - d0["mass_B"]) < 1e-5 * d0["mass_B"]
+
+
+# ---------------------------------------------------------------------------- beads
+def bead_case(cfg, seed=7, n_fil=6, n_b=4):
+    lo = [cfg.cx - cfg.a * 0.5, cfg.cy - cfg.b * 0.5, 2.5]
+    hi = [cfg.cx + cfg.a * 0.5, cfg.cy + cfg.b * 0.5, cfg.c * 0.6]
+    cen, dirs = inputs.random_filaments(seed, n_fil, n_b, cfg.d0, lo, hi, min_dist=2.05)
+    fil, pos, X = inputs.straight_filaments(cen, dirs, n_b, cfg.d0)
+    return fil, pos, X
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_beads_one_step_match_oracle(lbm, oracle, prec):
+    cfg = droplet_cfg(lbm, nx=48, ny=32, nz=20, prec=prec, max_beads=64, eps_coh=1.0 * 0.006,
+                      xi=0.02, gamma=1.0, a=18, b=11, c=14)
+    beads = bead_case(cfg)
+    sim, p, fR, fB, cot, acc, ob = run_pair(lbm, oracle, cfg, warm=5, steps=3, beads=beads)
+    X = sim.read(0, "bead_x")
+    V = sim.read(0, "bead_v")
+    F = sim.read(0, "bead_f")
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    assert np.allclose(X, ob.X, rtol=0, atol=tol * 10)
+    assert np.allclose(V, ob.V, rtol=0, atol=tol)
+    assert np.allclose(F, ob.F, rtol=0, atol=tol)
+    assert pop_err(sim.read(0, "populations"), fR, fB) < TOL[prec] * 10
+
+
+def test_fene_overstretch_reports_status(lbm, oracle):
+    cfg = droplet_cfg(lbm, prec="fp64", max_beads=8)
+    sim = lbm.Simulation([cfg])
+    sim.add_nanowires(0, 1, 4.0, np.array([[cfg.cx, cfg.cy, 5.0]]), np.array([[1.0, 0, 0]]))
+    X = sim.read(0, "bead_x")
+    X[1] = X[0] + np.array([2.6, 0, 0])
+    sim.write(0, "bead_x", X)
+    sim.step(1)
+    from paper_2607_06794_b300 import _lib
+    assert sim.status() == _lib.EFENE
+    sim.clear_error()
+    assert sim.status() == _lib.OK
+
+
+def test_nan_population_reports_status(lbm, oracle):
+    cfg = droplet_cfg(lbm, prec="fp32")
+    sim = lbm.Simulation([cfg])
+    f = sim.read(0, "populations")
+    f[0, 3, 5, 5, 5] = np.nan
+    sim.write(0, "populations", f)
+    sim.step(2)
+    from paper_2607_06794_b300 import _lib
+    assert sim.status() == _lib.ENAN
+
+
+# ---------------------------------------------------------------------------- descriptors
+def test_descriptors_match_oracle(lbm, oracle):
+    cfg = droplet_cfg(lbm, nx=64, ny=48, nz=24, prec="fp64", max_beads=400, a=24, b=18, c=16)
+    cfg = dataclasses.replace(cfg, x_src=20.0, x_snk=44.0)
+    sim = lbm.Simulation([cfg])
+    g = inputs.rng(3)
+    nw = 60
+    cen = np.c_[g.uniform(12, 52, nw), g.uniform(10, 38, nw), g.uniform(2, 10, nw)]
+    dirs = np.c_[g.normal(size=nw), g.normal(size=nw), 0.2 * g.normal(size=nw)]
+    sim.add_nanowires(0, nw, 8.0, cen, dirs)
+    X = sim_free_positions(cen, dirs, 4, cfg)
+    fil = np.repeat(np.arange(nw), 4)
+    pos = np.tile(np.arange(4), nw)
+    p = oracle_params(oracle, cfg)
+    sx, nc, perc, _ = oracle.descriptors(p, fil, pos, X, cfg.rcon, cfg.x_src, cfg.x_snk)
+    d = sim.descriptors(0)
+    assert d["n_beads"] == 4 * nw and d["n_bonds"] == 3 * nw
+    assert d["n_clusters"] == nc
+    assert bool(d["percolates"]) == perc
+    assert d["S_x"] == pytest.approx(sx, abs=1e-12)
+
+
+def test_random_nanowire_placement_is_valid(lbm, oracle):
+    cfg = droplet_cfg(lbm, nx=64, ny=32, nz=24, prec="fp32", max_beads=200, a=24, b=10, c=14)
+    sim = lbm.Simulation([cfg])
+    sim.add_nanowires(0, 20, 8.0, seed=99)
+    X = sim.read(0, "bead_x")
+    topo = sim.read(0, "bead_topo")
+    C = sim.read(0, "colour")
+    assert X.shape == (80, 3)
+    for k in range(len(X)):
+        x, y, z = np.rint(X[k]).astype(int)
+        assert C[z, y % cfg.ny, x % cfg.nx] > 0.9
+    # beads of different filaments further apart than d0
+    for a in range(len(X)):
+        for b in range(a + 1, len(X)):
+            if topo[a, 0] != topo[b, 0]:
+                d = X[b] - X[a]
+                d[0] -= cfg.nx * np.round(d[0] / cfg.nx)
+                d[1] -= cfg.ny * np.round(d[1] / cfg.ny)
+                assert np.linalg.norm(d) > cfg.d0
