@@ -203,8 +203,10 @@ static void moments(const orc_params* p, const double* fRs, const double* fBs, o
             jy += ey[i] * (a + b);
             jz += ez[i] * (a + b);
         }
-        m->rR[n] = p->rho0 * sR;
-        m->rB[n] = p->rho0 * sB;
+        /* Eq. (3) writes rho_k = rho0 sum_i f_i; the populations here carry
+         * density units (rho0 is their unit), so the sum is the density. */
+        m->rR[n] = sR;
+        m->rB[n] = sB;
         m->C[n] = (m->rR[n] - m->rB[n]) / (m->rR[n] + m->rB[n]);
         m->j[3 * n + 0] = jx;
         m->j[3 * n + 1] = jy;
