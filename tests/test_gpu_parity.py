@@ -230,3 +230,79 @@ def test_random_nanowire_placement_is_valid(lbm, oracle):
                 d[0] -= cfg.nx * np.round(d[0] / cfg.nx)
                 d[1] -= cfg.ny * np.round(d[1] / cfg.ny)
                 assert np.linalg.norm(d) > cfg.d0
+
+
+# ---------------------------------------------------------------------------- batching
+def test_batched_uneven_lattices_match_oracle_per_instance(lbm, oracle):
+    """Three lattices of different sizes in one handle advance like three oracle runs."""
+    cfgs = [droplet_cfg(lbm, nx=40, ny=24, nz=20, prec="fp64", J0=1e-3, evap_start=0),
+            droplet_cfg(lbm, nx=64, ny=16, nz=12, prec="fp64", theta_deg=100.0, sigma=0.02),
+            droplet_cfg(lbm, nx=24, ny=40, nz=9, prec="fp64", top_bc=0, J0=2e-3, evap_start=1)]
+    states = [oracle_state(oracle, c, 5) for c in cfgs]
+    sim = lbm.Simulation(cfgs)
+    for k, (p, fR, fB, cot) in enumerate(states):
+        sim.write(k, "populations", np.stack([fR, fB]))
+    accs = [oracle.Acc() for _ in cfgs]
+    for _ in range(4):
+        for (p, fR, fB, cot), acc in zip(states, accs):
+            oracle.step(p, fR, fB, cot, acc)
+    sim.step(4)
+    sim.sync()
+    for k, ((p, fR, fB, cot), acc) in enumerate(zip(states, accs)):
+        assert pop_err(sim.read(k, "populations"), fR, fB) < 1e-12, k
+        a = sim.read(k, "accum")
+        assert a[2] == pytest.approx(acc.evaporated, rel=1e-11, abs=1e-300)
+
+
+def test_batched_beads_in_two_instances(lbm, oracle):
+    cfgs = [droplet_cfg(lbm, nx=48, ny=32, nz=20, prec="fp64", max_beads=40, xi=0.02, a=18, b=11, c=14),
+            droplet_cfg(lbm, nx=32, ny=32, nz=16, prec="fp64", max_beads=40, xi=0.01, a=11, b=11, c=11,
+                        eps_coh=0.012)]
+    sim = lbm.Simulation(cfgs)
+    obs, states = [], []
+    for k, c in enumerate(cfgs):
+        p, fR, fB, cot = oracle_state(oracle, c, 3)
+        sim.write(k, "populations", np.stack([fR, fB]))
+        fil, pos, X = bead_case(c, seed=20 + k, n_fil=4)
+        cen = X.reshape(4, 4, 3).mean(axis=1)
+        dirs = X.reshape(4, 4, 3)[:, -1] - X.reshape(4, 4, 3)[:, 0]
+        sim.add_nanowires(k, 4, 8.0, cen, dirs)
+        obs.append(oracle.Beads(fil, pos, sim_free_positions(cen, dirs, 4, c)))
+        states.append((p, fR, fB, cot))
+    for _ in range(2):
+        for (p, fR, fB, cot), ob in zip(states, obs):
+            oracle.step(p, fR, fB, cot, oracle.Acc(), ob)
+    sim.step(2)
+    sim.sync()
+    for k, ((p, fR, fB, cot), ob) in enumerate(zip(states, obs)):
+        assert np.allclose(sim.read(k, "bead_x"), ob.X, atol=1e-11)
+        assert pop_err(sim.read(k, "populations"), fR, fB) < 1e-11
+
+
+# ---------------------------------------------------------------------------- full size
+def test_full_size_c2_step_in_bench_configuration(lbm, oracle):
+    """256x128x64 FP32 with 200 wires (the benchmark workload and launch configuration):
+    one step from the same oracle state, every population compared."""
+    from paper_2607_06794_b300 import workloads
+    wl = workloads.droplet_c2("fp32")
+    cfg = wl.cfgs[0]
+    p = oracle_params(oracle, cfg)
+    fR, fB = oracle.init_droplet(p, cfg.shape, cfg.cx, cfg.cy, cfg.cz, cfg.a, cfg.b, cfg.c, cfg.width)
+    cot = oracle.cot_map(wl.thetas[0])
+    sim = lbm.Simulation([cfg])
+    sim.set_substrate_pattern(0, wl.thetas[0])
+    sim.write(0, "populations", np.stack([fR, fB]))
+    lo = [cfg.cx - 0.6 * cfg.a, cfg.cy - 0.6 * cfg.b, 2.5]
+    hi = [cfg.cx + 0.6 * cfg.a, cfg.cy + 0.6 * cfg.b, 0.6 * cfg.c]
+    cen, dirs = inputs.random_filaments(cfg.seed, 200, 4, cfg.d0, lo, hi, min_dist=2.05)
+    sim.add_nanowires(0, 200, 8.0, cen, dirs)
+    fil, pos, X = inputs.straight_filaments(cen, dirs, 4, cfg.d0)
+    ob = oracle.Beads(fil, pos, sim_free_positions(cen, dirs, 4, cfg))
+    acc = oracle.Acc()
+    oracle.step(p, fR, fB, cot, acc, ob)
+    sim.step(1)
+    sim.sync()
+    assert pop_err(sim.read(0, "populations"), fR, fB) < TOL["fp32"] * 5
+    assert np.allclose(sim.read(0, "bead_x"), ob.X, atol=1e-6)
+    a = sim.read(0, "accum")
+    assert a[2] == pytest.approx(acc.evaporated, rel=1e-4)
