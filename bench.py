@@ -213,6 +213,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -243,6 +244,11 @@ def main():
     prec = wl.cfgs[0].prec
     sim = make_sim(wl)
     sim.step(args.warmup)
+    tuned = None
+    if not args.no_autotune:
+        # part of warm-up: real steps under each candidate tile shape
+        tuned = sim.autotune(3)
+        sim.step(3)
     sim.sync()
     if pg is not None:
         pg.barrier()
@@ -267,7 +273,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": tr, "peak_kind": peak_kind,
                 "kernel": "k_stream_collide", "ms_per_launch": round(ms_fluid, 5),
-                "alg_bytes_per_node": ALG_BYTES[prec], "kernel_src": kh}
+                "alg_bytes_per_node": ALG_BYTES[prec], "kernel_src": kh,
+                "ms_per_step_direct_launch": round(ms_prof_step, 5)}
     sim.sync()
 
     # end to end through the public API with host buffers
@@ -300,6 +307,9 @@ def main():
             w2 = workloads.droplet_c2(vp)
             s2 = make_sim(w2)
             s2.step(args.warmup)
+            if not args.no_autotune:
+                s2.autotune(3)
+                s2.step(3)
             s2.sync()
             m2 = barrier_max(time_steps(s2, args.steps))
             f2, _ = s2.profile_steps(args.steps)
@@ -329,7 +339,8 @@ def main():
                        "nanowires": wl.wires[0][0] if wl.wires[0] else 0,
                        "l2": "inputs larger than L2 (population buffers "
                              f"{2 * 19 * wl.nodes * {'fp64': 8, 'fp32': 4}.get(prec, 2) / 1e6:.0f} MB x2)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "tile_shape": None if tuned is None else tuned[0]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * steps_done_lp, "clocks": clocks, "variants": variants,
         }

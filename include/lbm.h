@@ -163,6 +163,14 @@ lbm_status lbm_step(lbm_handle* h, int n_steps);
  * fluid launch and per step. */
 lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, double* ms_step);
 
+/* Autotuner of the fused kernel's blocking (no paper counterpart): times
+ * every candidate tile shape (columns per block x z-chunk) on
+ * steps_per_candidate real time steps of this batch and keeps the fastest.
+ * Every candidate computes the same step, so the steps taken are ordinary
+ * steps of the run.  *chosen receives the candidate index and *best_ms the
+ * mean milliseconds of one fused launch (either may be NULL). */
+lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, double* best_ms);
+
 /* Wait for the stream and return the first latched device-side failure. */
 lbm_status lbm_sync(lbm_handle* h);
 

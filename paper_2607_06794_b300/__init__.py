@@ -152,6 +152,13 @@ class Simulation:
         _check(self.L.lbm_profile_steps(self.h, int(n), C.byref(a), C.byref(b)), "lbm_profile_steps")
         return a.value, b.value
 
+    def autotune(self, steps_per_candidate=5):
+        """Pick the fastest fused-kernel tile shape on real steps; returns (index, ms)."""
+        k, ms = C.c_int(), C.c_double()
+        _check(self.L.lbm_autotune(self.h, int(steps_per_candidate), C.byref(k), C.byref(ms)),
+               "lbm_autotune")
+        return k.value, ms.value
+
     def sync(self):
         _check(self.L.lbm_sync(self.h), "lbm_sync")
 

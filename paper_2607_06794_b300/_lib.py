@@ -15,7 +15,7 @@ FP64, FP32, FP16_SHIFTED, BF16_SHIFTED = range(4)
 
 # every entry point that include/lbm.h declares
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_substrate_pattern", "lbm_add_nanowires",
-           "lbm_step", "lbm_profile_steps", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
+           "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
            "lbm_deposit_descriptors", "lbm_destroy", "lbm_status_string")
 
 
@@ -69,6 +69,8 @@ def load():
     L.lbm_step.argtypes = [vp, C.c_int]
     L.lbm_profile_steps.restype = C.c_int
     L.lbm_profile_steps.argtypes = [vp, C.c_int, dp, dp]
+    L.lbm_autotune.restype = C.c_int
+    L.lbm_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), dp]
     L.lbm_sync.restype = C.c_int
     L.lbm_sync.argtypes = [vp]
     L.lbm_clear_error.restype = C.c_int

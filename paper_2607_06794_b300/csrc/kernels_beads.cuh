@@ -71,7 +71,7 @@ __device__ __forceinline__ long long tile_of(const InstDev& I, long long node) {
 
 // Step start: remember positions, flag the coupling tiles around every bead.
 __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
-    const InstDev& I = insts[blockIdx.y];
+    const InstDev I = insts[blockIdx.y];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= I.nb) return;
     double X[3];
@@ -96,21 +96,36 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
     for (int dy = -1; dy <= 2; ++dy)
         for (int dx = -1; dx <= 2; ++dx) {
             const int x = wrapi(fx + dx, I.nx), y = wrapi(fy + dy, I.ny);
-            for (int k = 0; k < nzt; ++k)
-                I.tflag[((long long)t8z[k] * I.t8y + (y >> 3)) * I.t8x + (x >> 3)] = 1;
+            for (int k = 0; k < nzt; ++k) {
+                const int t = (t8z[k] * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
+                if (atomicExch(I.tflag + t, 1u) == 0u) I.tlist[atomicAdd(I.tcount, 1)] = t;
+            }
         }
 }
 
 // u* = (j + (F_s + body)/2)/rho and grad C on the nodes of flagged tiles.
 template <class S>
+__device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobals* __restrict__ glob, int t);
+
+template <class S>
 __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ insts,
                                                     const StepGlobals* __restrict__ glob) {
     using T = typename S::T;
     using E = typename S::E;
-    const InstDev& I = insts[blockIdx.y];
-    const int ntile = I.t8x * I.t8y * I.t8z;
-    const int t = blockIdx.x;
-    if (t >= ntile || I.tflag == nullptr || !I.tflag[t] || I.nb == 0) return;
+    const InstDev* Ip = insts + blockIdx.y;
+    if (Ip->tflag == nullptr || Ip->nb == 0) return;
+    const int ntl = *Ip->tcount;
+    for (int it = blockIdx.x; it < ntl; it += gridDim.x) {
+        bead_field_tile<S>(Ip, glob, Ip->tlist[it]);
+        __syncthreads();
+    }
+}
+
+template <class S>
+__device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobals* __restrict__ glob, int t) {
+    using T = typename S::T;
+    using E = typename S::E;
+    const InstDev& I = *Ip;
     __shared__ T sC[12][12][12];
     __shared__ T sN[10][10][10][3];
     const long long step = __ldcg(&glob->step);
@@ -120,6 +135,7 @@ __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ 
     const long long N = I.N, cs = 19 * N;
     const int X0 = (t % I.t8x) * 8, Y0 = ((t / I.t8x) % I.t8y) * 8, Z0 = (t / (I.t8x * I.t8y)) * 8;
     const int tid = threadIdx.x;
+    __syncthreads();  // shared blocks of the previous tile are free
     for (int s = tid; s < 12 * 12 * 12; s += 512) {
         const int lx = s % 12, ly = (s / 12) % 12, lz = s / 144;
         const int z = Z0 - 2 + lz;
@@ -165,7 +181,7 @@ __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ 
     __syncthreads();
     const int lx = tid % 8, ly = (tid / 8) % 8, lz = tid / 64;
     const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
-    if (x >= nx || y >= ny || z >= nz) return;
+    if (x >= nx || y >= ny || z >= nz) return;  // the caller's barrier follows
     const long long node = ((long long)z * ny + y) * nx + x;
     // the sub-steps of this step accumulate the drag reaction here from zero
     T* fe = (T*)I.fext + 3 * node;
@@ -226,7 +242,7 @@ __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ 
 // Verlet neighbour list for the step: pairs closer than rlist that are not
 // bonded or bending partners (those are handled by index).
 __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
-    const InstDev& I = insts[blockIdx.y];
+    const InstDev I = insts[blockIdx.y];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= I.nb) return;
     const double xa = I.bx[3 * a], ya = I.bx[3 * a + 1], za = I.bx[3 * a + 2];
@@ -252,7 +268,7 @@ __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
 
 // First half kick and drift of the step
 __global__ void k_bead_kickdrift(const InstDev* __restrict__ insts) {
-    const InstDev& I = insts[blockIdx.y];
+    const InstDev I = insts[blockIdx.y];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= I.nb) return;
     const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
@@ -273,7 +289,7 @@ __global__ void k_bead_kickdrift(const InstDev* __restrict__ insts) {
 // last) the next first half kick and drift.
 template <typename T>
 __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
-    const InstDev& I = insts[blockIdx.y];
+    const InstDev I = insts[blockIdx.y];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= I.nb) return;
     const bool last = s == I.substeps;
@@ -379,7 +395,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
 // and reduces S_x, cluster count and percolation.
 // ---------------------------------------------------------------------------
 __global__ void k_desc_edges(const InstDev* __restrict__ insts, int only) {
-    const InstDev& I = insts[only];
+    const InstDev I = insts[only];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= I.nb) return;
     const double r2 = I.rcon * I.rcon;
@@ -399,7 +415,7 @@ __global__ void k_desc_edges(const InstDev* __restrict__ insts, int only) {
 }
 
 __global__ void __launch_bounds__(1024) k_desc_solve(const InstDev* __restrict__ insts, int only) {
-    const InstDev& I = insts[only];
+    const InstDev I = insts[only];
     const int n = I.nb;
     int* lab = I.lab;
     int* srcf = I.lab + I.nb_max;

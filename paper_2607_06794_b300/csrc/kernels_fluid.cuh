@@ -58,7 +58,22 @@ __device__ T colour_ext(const InstDev& I, const T* __restrict__ rho, int x, int 
 // halo into which every stored population is pushed to the node it streams
 // to next step.  Fully interior nodes are stored plainly; tile-edge and halo
 // nodes are added atomically (their buffer was zeroed one step earlier).
+// Per plane: [pull loads of plane z; flush plane z-2; C of plane z+2] |
+// [normals of plane z+1] | [collide plane z, store, push].
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_near(int a, int n) {
+    while (a < 0) a += n;
+    while (a >= n) a -= n;
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ T inv_norm(T g2);
+template <>
+__device__ __forceinline__ float inv_norm<float>(float g2) { return rsqrtf(g2); }
+template <>
+__device__ __forceinline__ double inv_norm<double>(double g2) { return 1.0 / sqrt(g2); }
+
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
     k_stream_collide(const InstDev* __restrict__ insts, const TileDesc* __restrict__ tiles,
@@ -75,20 +90,25 @@ __global__ void __launch_bounds__(TX * TY)
     __shared__ int sErr;
 
     const TileDesc td = tiles[blockIdx.x];
-    const InstDev& I = insts[td.inst];
-    const int nx = I.nx, ny = I.ny, nz = I.nz, top_bc = I.top_bc;
-    const long long N = I.N;
-    const long long cs = 19 * N;
+    const InstDev& Ig = insts[td.inst];
+    const int nx = Ig.nx, ny = Ig.ny, nz = Ig.nz, top_bc = Ig.top_bc;
+    const unsigned nxy = (unsigned)nx * ny;
+    const unsigned N = (unsigned)Ig.N;
+    const unsigned cs = 19u * N;
     const long long step = __ldcg(&glob->step);
     const int pa = (int)(step & 1);
     const int pr = (int)(step % 3);
-    const E* __restrict__ src = (const E*)I.pop[pa];
-    E* __restrict__ dst = (E*)I.pop[pa ^ 1];
-    const T* __restrict__ rho_r = (const T*)I.rho[pr];
-    T* __restrict__ rho_w = (T*)I.rho[(pr + 1) % 3];
-    T* __restrict__ rho_z = (T*)I.rho[(pr + 2) % 3];
-    T* __restrict__ fext = (T*)I.fext;
-    const unsigned char* __restrict__ tflag = I.tflag;
+    const E* __restrict__ src = (const E*)Ig.pop[pa];
+    E* __restrict__ dst = (E*)Ig.pop[pa ^ 1];
+    const T* __restrict__ rho_r = (const T*)Ig.rho[pr];
+    T* __restrict__ rho_w = (T*)Ig.rho[(pr + 1) % 3];
+    T* __restrict__ rho_z = (T*)Ig.rho[(pr + 2) % 3];
+    const T* __restrict__ fext = (const T*)Ig.fext;
+    const unsigned* __restrict__ tflag = Ig.tflag;
+    const double* __restrict__ cotm = Ig.cot;
+    double* accp = Ig.acc;
+    int* errp = Ig.err;
+    const int t8x = Ig.t8x, t8y = Ig.t8y;
 
     const int x0 = td.x0, y0 = td.y0, z0 = td.z0, z1 = td.z1;
     const int tw = min(TX, nx - x0), th = min(TY, ny - y0);
@@ -97,34 +117,66 @@ __global__ void __launch_bounds__(TX * TY)
     const bool active = tx < tw && ty < th;
     const int x = x0 + tx, y = y0 + ty;
 
-    const T rho0 = (T)I.rho0, tauR = (T)I.tau_R, tauB = (T)I.tau_B, beta = (T)I.beta;
-    const T hsig = T(0.5) * (T)I.sigma;
-    const T bfx = (T)I.body[0], bfy = (T)I.body[1], bfz = (T)I.body[2];
-    const bool evap_on = I.J0 > 0.0 && I.evap_start >= 0 && step >= I.evap_start && I.acc[1] > 0.0;
-    const T J0 = (T)I.J0, Kk = (T)I.K, inv_h0 = evap_on ? (T)(1.0 / I.acc[1]) : T(0);
+    const T rho0 = (T)Ig.rho0, itR = T(1) / (T)Ig.tau_R, itB = T(1) / (T)Ig.tau_B;
+    const T beta = (T)Ig.beta;
+    const T hsig = T(0.5) * (T)Ig.sigma;
+    const T bfx = (T)Ig.body[0], bfy = (T)Ig.body[1], bfz = (T)Ig.body[2];
+    const double h0 = accp[1];
+    const bool evap_on = Ig.J0 > 0.0 && Ig.evap_start >= 0 && step >= Ig.evap_start && h0 > 0.0;
+    const T J0 = (T)Ig.J0, Kk = (T)Ig.K, inv_h0 = evap_on ? (T)(1.0 / h0) : T(0);
 
     auto ring = [](int q) { return ((q % 3) + 3) % 3; };
+    auto colour = [&](unsigned n) {
+        const T a = rho_r[n], b = rho_r[N + n];
+        return (a - b) / (a + b);
+    };
+    // wetting ghost colour below z = 0 (flat-wall geometric form, D2Q9 weights)
+    auto ghost = [&](int gx, int gy) {
+        T ax = 0, ay = 0;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int k = (dx != 0) + (dy != 0);
+                const T w = k == 0 ? T(4.0 / 9.0) : (k == 1 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+                const T c = colour((unsigned)wrap_near(gy + dy, ny) * nx + wrap_near(gx + dx, nx));
+                ax += w * dx * c;
+                ay += w * dy * c;
+            }
+        ax *= T(3);
+        ay *= T(3);
+        T g = colour((unsigned)gy * nx + gx) + (T)cotm[gy * nx + gx] * sqrt(ax * ax + ay * ay);
+        return g > T(1) ? T(1) : (g < T(-1) ? T(-1) : g);
+    };
 
     // liquid column height of this thread's column, h = sum_z (1+C)/2 (Eq. (8))
     T hcol = 0;
     if (evap_on && active) {
-        for (int z = 0; z < nz; ++z) {
-            const long long n = ((long long)z * ny + y) * nx + x;
-            hcol += (T(1) + colour_of(rho_r, N, n)) / T(2);
+        const unsigned c0 = (unsigned)y * nx + x;
+        int z = 0;
+        for (; z + 4 <= nz; z += 4) {
+            T c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = colour(c0 + (unsigned)(z + k) * nxy);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hcol += (T(1) + c[k]) / T(2);
         }
+        for (; z < nz; ++z) hcol += (T(1) + colour(c0 + (unsigned)z * nxy)) / T(2);
     }
 
     for (int s = tid; s < 3 * HY1 * HX1 * 2; s += NT) (&sA[0][0][0][0])[s] = T(0);
     if (tid == 0) sErr = 0;
 
-    // C of plane p into the ring, over the window of the tile plus 2 cells
+    // C of plane p into the ring over the tile plus 2 cells
     auto loadC = [&](int p) {
         if (p < -1 || p > nz) return;
         const int r = ring(p);
+        const int pz = p >= nz ? nz - 1 : p;
         for (int s = tid; s < HX2 * HY2; s += NT) {
-            const int sy = s / HX2, sx = s % HX2;
+            const int sy = s / HX2, sx = s - sy * HX2;
             if (sx > tw + 3 || sy > th + 3) continue;
-            sC[r][sy][sx] = colour_ext<T>(I, rho_r, x0 - 2 + sx, y0 - 2 + sy, p);
+            const int gx = wrap_near(x0 - 2 + sx, nx), gy = wrap_near(y0 - 2 + sy, ny);
+            sC[r][sy][sx] = p < 0 ? ghost(gx, gy) : colour((unsigned)pz * nxy + (unsigned)gy * nx + gx);
         }
     };
     // gradient and unit normal of plane q over the tile plus 1 cell
@@ -133,7 +185,7 @@ __global__ void __launch_bounds__(TX * TY)
         if (q >= 0 && q < nz) {
             const int rm = ring(q - 1), r0 = ring(q), rp = ring(q + 1);
             for (int s = tid; s < HX1 * HY1; s += NT) {
-                const int sy = s / HX1, sx = s % HX1;
+                const int sy = s / HX1, sx = s - sy * HX1;
                 if (sx > tw + 1 || sy > th + 1) continue;
                 T gx = 0, gy = 0, gz = 0;
 #pragma unroll
@@ -141,20 +193,22 @@ __global__ void __launch_bounds__(TX * TY)
                     const int rr = cz(i) < 0 ? rm : (cz(i) > 0 ? rp : r0);
                     const T c = sC[rr][sy + 1 + cy(i)][sx + 1 + cx(i)];
                     const T w = (T)wq(i);
-                    gx += w * cx(i) * c;
-                    gy += w * cy(i) * c;
-                    gz += w * cz(i) * c;
+                    if (cx(i)) gx += w * cx(i) * c;
+                    if (cy(i)) gy += w * cy(i) * c;
+                    if (cz(i)) gz += w * cz(i) * c;
                 }
                 gx *= T(3);
                 gy *= T(3);
                 gz *= T(3);
-                const T g = sqrt(gx * gx + gy * gy + gz * gz);
-                if (g > T(1e-8)) {
-                    sN[rq][sy][sx][0] = gx / g;
-                    sN[rq][sy][sx][1] = gy / g;
-                    sN[rq][sy][sx][2] = gz / g;
+                const T g2 = gx * gx + gy * gy + gz * gz;
+                T* nn = sN[rq][sy][sx];
+                if (g2 > T(1e-16)) {
+                    const T ig = inv_norm<T>(g2);
+                    nn[0] = gx * ig;
+                    nn[1] = gy * ig;
+                    nn[2] = gz * ig;
                 } else {
-                    sN[rq][sy][sx][0] = sN[rq][sy][sx][1] = sN[rq][sy][sx][2] = T(0);
+                    nn[0] = nn[1] = nn[2] = T(0);
                 }
                 if (sx >= 1 && sx <= tw && sy >= 1 && sy <= th) {
                     T* G = sG[q & 1][sy - 1][sx - 1];
@@ -173,25 +227,19 @@ __global__ void __launch_bounds__(TX * TY)
     double evap_sum = 0.0, top_in = 0.0, top_out = 0.0;
     int err = 0;
 
-    // push a post-collision pair into the accumulator ring
-    auto push = [&](int sx, int sy, int q, T r, T b) {
-        T* a = sA[ring(q)][sy][sx];
-        atomicAdd(a, r);
-        atomicAdd(a + 1, b);
-    };
-
     // flush the completed accumulator plane q to global memory
     auto flush = [&](int q) {
+        if (q < z0 - 1) return;  // nothing was pushed below the halo plane
         const int r = ring(q);
         for (int s = tid; s < HX1 * HY1; s += NT) {
-            const int sy = s / HX1, sx = s % HX1;
+            const int sy = s / HX1, sx = s - sy * HX1;
             if (sx > tw + 1 || sy > th + 1) continue;
             const T a0 = sA[r][sy][sx][0], a1 = sA[r][sy][sx][1];
             sA[r][sy][sx][0] = T(0);
             sA[r][sy][sx][1] = T(0);
             if (q < 0 || q >= nz) continue;
-            const int gx = wrapi(x0 - 1 + sx, nx), gy = wrapi(y0 - 1 + sy, ny);
-            const long long n = ((long long)q * ny + gy) * nx + gx;
+            const int gx = wrap_near(x0 - 1 + sx, nx), gy = wrap_near(y0 - 1 + sy, ny);
+            const unsigned n = (unsigned)q * nxy + (unsigned)gy * nx + gx;
             const bool core = sx >= 1 && sx <= tw && sy >= 1 && sy <= th && q >= z0 && q < z1;
             const bool interior = core && sx > 1 && sx < tw && sy > 1 && sy < th &&
                                   !(q == z0 && z0 > 0) && !(q == z1 - 1 && z1 < nz);
@@ -209,6 +257,11 @@ __global__ void __launch_bounds__(TX * TY)
         }
     };
 
+    // neighbour columns of this thread (pull sources) as row/column offsets
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const unsigned rowm = (unsigned)ym * nx, row0 = (unsigned)y * nx, rowp = (unsigned)yp * nx;
+
     // ---- prologue: C planes and normals below the first plane ----
     if (z0 == 0) {
         loadC(-1);
@@ -218,7 +271,6 @@ __global__ void __launch_bounds__(TX * TY)
         computeN(0);
         __syncthreads();
         computeN(-1);
-        __syncthreads();
     } else {
         loadC(z0 - 2);
         loadC(z0 - 1);
@@ -229,60 +281,36 @@ __global__ void __launch_bounds__(TX * TY)
         loadC(z0 + 1);
         __syncthreads();
         computeN(z0);
-        __syncthreads();
     }
+    __syncthreads();
 
     for (int z = z0; z < z1; ++z) {
-        loadC(z + 2);
-        __syncthreads();
-        computeN(z + 1);
-        __syncthreads();
-
+        // ---- phase 1: pull loads of plane z (consumed in phase 3), flush, next C ----
+        T Fi[19];
+        T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+        const unsigned node = (unsigned)z * nxy + row0 + x;
         if (active) {
-            const long long node = ((long long)z * ny + y) * nx + x;
-            // curvature kappa = -3 sum_i w_i c_i . n(x + c_i)
-            T kap = 0;
-#pragma unroll
-            for (int i = 1; i < 19; ++i) {
-                const T* nn = sN[ring(z + cz(i))][ty + 1 + cy(i)][tx + 1 + cx(i)];
-                kap += (T)wq(i) * (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]);
-            }
-            kap *= T(-3);
-            const T* G = sG[z & 1][ty][tx];
-            const T Gx = G[0], Gy = G[1], Gz = G[2];
-            T Fx = hsig * kap * Gx + bfx, Fy = hsig * kap * Gy + bfy, Fz = hsig * kap * Gz + bfz;
-            if (tflag != nullptr &&
-                tflag[((z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3)]) {
-                const T* fe = fext + 3 * node;
-                Fx += fe[0];
-                Fy += fe[1];
-                Fz += fe[2];
-            }
-
-            // pull-stream with half-way bounce-back at the wall and the gas plane on top
-            T Fi[19];
-            T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
                 const int sz = z - cz(i);
                 T r, b;
                 if (sz < 0 || (sz >= nz && top_bc == 0)) {
-                    S::load(src, cs, (long long)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
+                    S::load(src, cs, (unsigned)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
                 } else if (sz >= nz) {
                     r = T(0);
                     b = (T)wq(i) * rho0;
                     top_in += (double)b;
                 } else {
-                    const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
-                    S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx,
-                            (T)wq(i), rho0, r, b);
+                    const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
+                    const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
+                    S::load(src, cs, (unsigned)i * N + (unsigned)sz * nxy + row + sx, (T)wq(i), rho0, r, b);
                 }
                 rR += r;
                 rB += b;
                 Fi[i] = r + b;
-                jx += cx(i) * Fi[i];
-                jy += cy(i) * Fi[i];
-                jz += cz(i) * Fi[i];
+                if (cx(i)) jx += cx(i) * Fi[i];
+                if (cy(i)) jy += cy(i) * Fi[i];
+                if (cz(i)) jz += cz(i) * Fi[i];
             }
             if (z == nz - 1 && top_bc == 1) {
                 // what left the domain through the top in this stream
@@ -290,41 +318,71 @@ __global__ void __launch_bounds__(TX * TY)
                 for (int i = 0; i < 19; ++i)
                     if (cz(i) > 0) {
                         T r, b;
-                        S::load(src, cs, (long long)i * N + node, (T)wq(i), rho0, r, b);
+                        S::load(src, cs, (unsigned)i * N + node, (T)wq(i), rho0, r, b);
                         top_out += (double)r + (double)b;
                     }
             }
-
+        }
+        flush(z - 2);
+        loadC(z + 2);
+        __syncthreads();
+        // ---- phase 2: normals of plane z+1 ----
+        computeN(z + 1);
+        __syncthreads();
+        // ---- phase 3: collide, recolour, evaporate, store, push ----
+        if (active) {
+            T kap = 0;
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const T* nn = sN[ring(z + cz(i))][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                T d = 0;
+                if (cx(i)) d += cx(i) * nn[0];
+                if (cy(i)) d += cy(i) * nn[1];
+                if (cz(i)) d += cz(i) * nn[2];
+                kap += (T)wq(i) * d;
+            }
+            kap *= T(-3);
+            const T* G = sG[z & 1][ty][tx];
+            const T Gx = G[0], Gy = G[1], Gz = G[2];
+            T Fx = hsig * kap * Gx + bfx, Fy = hsig * kap * Gy + bfy, Fz = hsig * kap * Gz + bfz;
+            if (tflag != nullptr && tflag[((z >> 3) * t8y + (y >> 3)) * t8x + (x >> 3)]) {
+                const T* fe = fext + 3 * (size_t)node;
+                Fx += fe[0];
+                Fy += fe[1];
+                Fz += fe[2];
+            }
             const T rho = rR + rB;
             if (!(rho > T(0))) err |= ERR_NAN;
-            const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho,
-                    uz = (jz + T(0.5) * Fz) / rho;
-            const T omega = (rR / rho) / tauR + (rB / rho) / tauB;
+            const T irho = T(1) / rho;
+            const T ux = (jx + T(0.5) * Fx) * irho, uy = (jy + T(0.5) * Fy) * irho,
+                    uz = (jz + T(0.5) * Fz) * irho;
+            const T phi = rR * irho;
+            const T omega = phi * itR + (rB * irho) * itB;
             const T usq = ux * ux + uy * uy + uz * uz;
             const T uF = ux * Fx + uy * Fy + uz * Fz;
             const T gsrc = T(1) - T(0.5) * omega;
-            const T gm = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
-            const bool hasg = gm > T(1e-8);
-            const T ig = hasg ? T(1) / gm : T(0);
-            const T phi = rR / rho;
-            const T coef = beta * (rR * rB / rho);
+            const T g2 = Gx * Gx + Gy * Gy + Gz * Gz;
+            const bool hasg = g2 > T(1e-16);
+            const T ig = hasg ? inv_norm<T>(g2) : T(0);
+            const T gm = g2 * ig;
+            const T coef = beta * (rR * rB * irho);
             T dm = 0;
             if (evap_on) {
                 const T ht = hcol * inv_h0;
                 if (ht > T(0)) dm = J0 / (Kk + ht) * T(0.5) * gm;
             }
+            const T rGx = Gx * ig, rGy = Gy * ig, rGz = Gz * ig;
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
                 const T w = (T)wq(i);
-                const T cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+                T cu = 0, cF = 0, cG = 0;
+                if (cx(i)) { cu += cx(i) * ux; cF += cx(i) * Fx; cG += cx(i) * rGx; }
+                if (cy(i)) { cu += cy(i) * uy; cF += cy(i) * Fy; cG += cy(i) * rGy; }
+                if (cz(i)) { cu += cz(i) * uz; cF += cz(i) * Fz; cG += cz(i) * rGz; }
                 const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
-                const T cF = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
                 const T Sg = gsrc * w * (T(3) * (cF - uF) + T(9) * cu * cF);
                 const T post = Fi[i] - omega * (Fi[i] - feq) + Sg;
-                const T cph = (i > 0 && hasg)
-                                  ? (cx(i) * Gx + cy(i) * Gy + cz(i) * Gz) * (T)inv_len(i) * ig
-                                  : T(0);
-                T r = phi * post + coef * w * cph;
+                T r = phi * post + coef * w * (cG * (T)inv_len(i));
                 T b = post - r;
                 if (i == 0 && evap_on) {
                     T d = dm > r ? r : dm;
@@ -334,12 +392,18 @@ __global__ void __launch_bounds__(TX * TY)
                     evap_sum += (double)d;
                 }
                 T rq, bq;
-                S::store(dst, cs, (long long)i * N + node, w, rho0, r, b, rq, bq);
+                S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
                 const int tz = z + cz(i);
-                if (tz < 0 || (tz >= nz && top_bc == 0)) {
-                    push(tx + 1, ty + 1, z, rq, bq);  // bounces back to this node
-                } else if (tz < nz) {
-                    push(tx + 1 + cx(i), ty + 1 + cy(i), tz, rq, bq);
+                T* a;
+                if (tz < 0 || (tz >= nz && top_bc == 0))
+                    a = sA[ring(z)][ty + 1][tx + 1];  // bounces back to this node
+                else if (tz < nz)
+                    a = sA[ring(tz)][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                else
+                    a = nullptr;
+                if (a) {
+                    atomicAdd(a, rq);
+                    atomicAdd(a + 1, bq);
                 }
             }
             if (z == nz - 1 && top_bc == 1) {
@@ -348,15 +412,14 @@ __global__ void __launch_bounds__(TX * TY)
 #pragma unroll
                 for (int i = 0; i < 19; ++i)
                     if (cz(i) < 0) inB += (T)wq(i) * rho0;
-                push(tx + 1, ty + 1, z, T(0), inB);
+                atomicAdd(&sA[ring(z)][ty + 1][tx + 1][1], inB);
             }
         }
         __syncthreads();
-        flush(z - 1);
     }
-    __syncthreads();
+    // the remaining planes touch disjoint ring slots
+    flush(z1 - 2);
     flush(z1 - 1);
-    __syncthreads();
     flush(z1);
 
     // ---- block sums of the FP64 budgets ----
@@ -371,10 +434,10 @@ __global__ void __launch_bounds__(TX * TY)
     if (tid < 3) {
         double s = 0.0;
         for (int w = 0; w < NT / 32; ++w) s += sRed[w][tid];
-        if (s != 0.0) atomicAdd(I.acc + 2 + tid, s);
+        if (s != 0.0) atomicAdd(accp + 2 + tid, s);
     }
     if (tid == 0) {
-        if (sErr) atomicOr(I.err, sErr);
+        if (sErr) atomicOr(errp, sErr);
         // the last block to finish advances the step counter
         __threadfence();
         const unsigned t = atomicAdd(&glob->done, 1u);

@@ -17,8 +17,14 @@ using namespace lbm;
 
 namespace {
 
-constexpr int TILE_X = 32;
-constexpr int TILE_Y = 8;
+// Tile shapes of the fused kernel the autotuner chooses from (columns x-by-y,
+// then a z-chunk per block; chunk 0 means "split until the GPU is filled").
+struct Shape {
+    int tx, ty, chunk;
+};
+const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {64, 4, 0}, {64, 4, 16},
+                        {32, 4, 0}, {32, 4, 16}, {64, 8, 0}, {64, 8, 32}};
+constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 64;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
 
@@ -49,19 +55,20 @@ struct Layout {
     int ntiles = 0;
 };
 
-int chunk_z(const lbm_config& c) {
-    // z-chunk of the fused kernel: enough blocks to fill the GPU on small lattices
-    const long long cols = (long long)((c.nx + TILE_X - 1) / TILE_X) * ((c.ny + TILE_Y - 1) / TILE_Y);
+int chunk_z(const lbm_config& c, const Shape& sh) {
+    if (sh.chunk > 0) return std::max(2, std::min(sh.chunk, c.nz));
+    // enough blocks to fill the GPU on small lattices
+    const long long cols = (long long)((c.nx + sh.tx - 1) / sh.tx) * ((c.ny + sh.ty - 1) / sh.ty);
     int ch = c.nz;
     while (cols * ((c.nz + ch - 1) / ch) < 4 * 148 && ch > 8) ch = (ch + 1) / 2;
     return std::max(2, std::min(ch, c.nz));
 }
 
-std::vector<TileDesc> make_tiles(const lbm_config* cfgs, int n) {
+std::vector<TileDesc> make_tiles(const lbm_config* cfgs, int n, const Shape& sh) {
     std::vector<TileDesc> t;
     for (int k = 0; k < n; ++k) {
         const lbm_config& c = cfgs[k];
-        const int ch = chunk_z(c);
+        const int ch = chunk_z(c, sh);
         std::vector<std::pair<int, int>> zr;
         for (int z0 = 0; z0 < c.nz;) {
             int z1 = std::min(c.nz, z0 + ch);
@@ -70,8 +77,8 @@ std::vector<TileDesc> make_tiles(const lbm_config* cfgs, int n) {
             z0 = z1;
         }
         for (auto& r : zr)
-            for (int y0 = 0; y0 < c.ny; y0 += TILE_Y)
-                for (int x0 = 0; x0 < c.nx; x0 += TILE_X)
+            for (int y0 = 0; y0 < c.ny; y0 += sh.ty)
+                for (int x0 = 0; x0 < c.nx; x0 += sh.tx)
                     t.push_back(TileDesc{k, x0, y0, r.first, r.second, 0, 0, 0});
     }
     return t;
@@ -81,9 +88,9 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
     L.inst.assign(n, InstDev{});
     L.glob = (StepGlobals*)cv.take(sizeof(StepGlobals));
     L.d_inst = (InstDev*)cv.take(sizeof(InstDev) * n);
-    std::vector<TileDesc> tiles = make_tiles(cfgs, n);
-    L.ntiles = (int)tiles.size();
-    L.d_tiles = (TileDesc*)cv.take(sizeof(TileDesc) * tiles.size());
+    size_t maxt = 0;
+    for (int k = 0; k < NSHAPES; ++k) maxt = std::max(maxt, make_tiles(cfgs, n, SHAPES[k]).size());
+    L.d_tiles = (TileDesc*)cv.take(sizeof(TileDesc) * maxt);
     size_t need_stage = 0;
     for (int k = 0; k < n; ++k) {
         const lbm_config& c = cfgs[k];
@@ -109,7 +116,9 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.fext = cv.take(3 * I.N * cb);
             I.ust = cv.take(3 * I.N * cb);
             I.gcol = cv.take(3 * I.N * cb);
-            I.tflag = (unsigned char*)cv.take((size_t)I.t8x * I.t8y * I.t8z);
+            I.tflag = (unsigned*)cv.take(sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int));
+            I.tcount = (int*)(I.tflag ? I.tflag + (size_t)I.t8x * I.t8y * I.t8z : nullptr);
+            I.tlist = (int*)cv.take(sizeof(int) * (size_t)I.t8x * I.t8y * I.t8z);
             const size_t vb = sizeof(double) * 3 * c.max_beads;
             I.bx = (double*)cv.take(vb);
             I.bv = (double*)cv.take(vb);
@@ -135,7 +144,8 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
 
 lbm_status check_config(const lbm_config& c) {
     if (c.nx < 1 || c.ny < 1 || c.nz < 2) return LBM_EINVAL;
-    if ((long long)c.nx * c.ny * c.nz > (1LL << 31)) return LBM_EINVAL;
+    // 32-bit element offsets inside one population buffer: 38 N < 2^32
+    if ((long long)c.nx * c.ny * c.nz * 38 >= (1LL << 32)) return LBM_EINVAL;
     if (c.prec < LBM_FP64 || c.prec > LBM_BF16_SHIFTED) return LBM_EINVAL;
     if (!(c.tau_R > 0.5) || !(c.tau_B > 0.5)) return LBM_EINVAL;
     if (!(c.rho0 > 0.0) || c.beta < 0.0 || c.beta > 1.0 || c.sigma < 0.0) return LBM_EINVAL;
@@ -170,6 +180,7 @@ struct lbm_handle {
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
     int max_nb = 0;
+    int shape = 0;  // index into SHAPES
 };
 
 #define CK(x)                                   \
@@ -184,9 +195,33 @@ namespace {
 
 template <class S>
 lbm_status launch_fused(lbm_handle* h) {
-    k_stream_collide<S, TILE_X, TILE_Y><<<h->L.ntiles, TILE_X * TILE_Y, 0, h->stream>>>(
-        h->L.d_inst, h->L.d_tiles, h->L.glob);
+    const Shape& sh = SHAPES[h->shape];
+    const int nb = h->L.ntiles;
+    const InstDev* in = h->L.d_inst;
+    const TileDesc* td = h->L.d_tiles;
+    if (sh.tx == 32 && sh.ty == 8)
+        k_stream_collide<S, 32, 8><<<nb, 256, 0, h->stream>>>(in, td, h->L.glob);
+    else if (sh.tx == 64 && sh.ty == 4)
+        k_stream_collide<S, 64, 4><<<nb, 256, 0, h->stream>>>(in, td, h->L.glob);
+    else if (sh.tx == 32 && sh.ty == 4)
+        k_stream_collide<S, 32, 4><<<nb, 128, 0, h->stream>>>(in, td, h->L.glob);
+    else if constexpr (sizeof(typename S::T) == 4)
+        k_stream_collide<S, 64, 8><<<nb, 512, 0, h->stream>>>(in, td, h->L.glob);
+    else
+        return LBM_EINVAL;
     CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// select a tile shape: rebuild and upload the tile table
+lbm_status set_shape(lbm_handle* h, int k) {
+    std::vector<TileDesc> tiles = make_tiles(h->cfg.data(), (int)h->cfg.size(), SHAPES[k]);
+    CK(cudaMemcpyAsync(h->L.d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->L.ntiles = (int)tiles.size();
+    h->shape = k;
+    h->graph_dirty = true;
     return LBM_OK;
 }
 
@@ -198,14 +233,16 @@ lbm_status launch_beads(lbm_handle* h) {
     // clear all coupling-tile flags (contiguous per instance; one memset each)
     for (int k = 0; k < n; ++k) {
         const InstDev& I = h->L.inst[k];
-        if (I.tflag) CK(cudaMemsetAsync(I.tflag, 0, (size_t)I.t8x * I.t8y * I.t8z, h->stream));
+        if (I.tflag)
+            CK(cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int),
+                               h->stream));
     }
     const int bt = 128;
     const dim3 gb((h->max_nb + bt - 1) / bt, n);
     k_bead_begin<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
     int maxt = 0;
     for (auto& I : h->L.inst) maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
-    k_bead_field<S><<<dim3(maxt, n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
+    k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
     k_bead_nlist<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
     k_bead_kickdrift<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
     const int S_ = h->cfg[0].substeps;
@@ -543,10 +580,7 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
         return s;
     };
     if (cudaMemsetAsync(h->L.glob, 0, sizeof(StepGlobals), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
-    std::vector<TileDesc> tiles = make_tiles(cfgs, n);
-    if (cudaMemcpyAsync(h->L.d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice,
-                        h->stream) != cudaSuccess)
-        return fail(LBM_ECUDA);
+    if (set_shape(h, 0) != LBM_OK) return fail(LBM_ECUDA);
     for (int k = 0; k < n; ++k) {
         const lbm_config& c = h->cfg[k];
         InstDev& I = h->L.inst[k];
@@ -592,7 +626,8 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
             if (cudaMemsetAsync(I.fext, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
                 cudaMemsetAsync(I.ust, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
                 cudaMemsetAsync(I.gcol, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
-                cudaMemsetAsync(I.tflag, 0, (size_t)I.t8x * I.t8y * I.t8z, h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int),
+                                h->stream) != cudaSuccess ||
                 cudaMemsetAsync(I.bF, 0, sizeof(double) * 3 * c.max_beads, h->stream) != cudaSuccess)
                 return fail(LBM_ECUDA);
         }
@@ -760,6 +795,30 @@ lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, doubl
     for (auto& e : ev) cudaEventDestroy(e);
     (void)cudaGetLastError();
     return st;
+}
+
+lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, double* best_ms) {
+    if (!h || steps_per_candidate < 1) return LBM_EINVAL;
+    int best = -1;
+    double bt = 1e300;
+    for (int k = 0; k < NSHAPES; ++k) {
+        if (h->prec == LBM_FP64 && SHAPES[k].tx * SHAPES[k].ty > 256) continue;
+        lbm_status st = set_shape(h, k);
+        if (st != LBM_OK) return st;
+        double f = 0, s = 0;
+        st = lbm_profile_steps(h, 1, &f, &s);  // first launch of this shape: untimed
+        if (st == LBM_OK) st = lbm_profile_steps(h, steps_per_candidate, &f, &s);
+        if (st != LBM_OK) return st;
+        if (f < bt) {
+            bt = f;
+            best = k;
+        }
+    }
+    lbm_status st = set_shape(h, best);
+    if (st != LBM_OK) return st;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = bt;
+    return LBM_OK;
 }
 
 lbm_status lbm_sync(lbm_handle* h) {

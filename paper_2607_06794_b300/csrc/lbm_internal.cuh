@@ -48,12 +48,12 @@ enum : int { ERR_NAN = 1, ERR_FENE = 2, ERR_BEAD = 4, ERR_TIMEOUT = 8, ERR_CAP =
 struct StoreF64 {
     using T = double;
     using E = double;
-    static __device__ __forceinline__ void load(const E* __restrict__ p, long long cs, long long k,
+    static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         r = __ldg(p + k);
         b = __ldg(p + cs + k);
     }
-    static __device__ __forceinline__ void store(E* __restrict__ p, long long cs, long long k, T w,
+    static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         p[k] = r;
         p[cs + k] = b;
@@ -75,12 +75,12 @@ struct StoreF64 {
 struct StoreF32 {
     using T = float;
     using E = float;
-    static __device__ __forceinline__ void load(const E* __restrict__ p, long long cs, long long k,
+    static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         r = __ldg(p + k);
         b = __ldg(p + cs + k);
     }
-    static __device__ __forceinline__ void store(E* __restrict__ p, long long cs, long long k, T w,
+    static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         p[k] = r;
         p[cs + k] = b;
@@ -129,13 +129,13 @@ struct StoreShift16 {
         r = (psi + 0.5f) * F;
         b = F - r;
     }
-    static __device__ __forceinline__ void load(const E* __restrict__ p, long long cs, long long k,
+    static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         float P = Cvt<H>::f(p[k]);
         float psi = Cvt<H>::f(p[cs + k]);
         decode(P, psi, w, rho0, r, b);
     }
-    static __device__ __forceinline__ void store(E* __restrict__ p, long long cs, long long k, T w,
+    static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         float F = r + b;
         H qP = Cvt<H>::h(F - w * rho0);
@@ -174,7 +174,9 @@ struct InstDev {
     void* fext;                  // [N][3] bead force on the fluid (compute type)
     void* ust;                   // [N][3] u* near beads (compute type)
     void* gcol;                  // [N][3] grad C near beads (compute type)
-    unsigned char* tflag;        // [t8z][t8y][t8x] coupling-tile flags
+    unsigned* tflag;             // [t8z][t8y][t8x] coupling-tile flags
+    int* tlist;                  // flagged tiles of this step (compact)
+    int* tcount;                 // number of entries in tlist
     double* cot;                 // [ny][nx] cot(theta)
     double* acc;                 // [8]: step, h0, evaporated, top_in, top_out, ...
     int* err;                    // latched error bits
