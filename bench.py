@@ -323,6 +323,26 @@ def main():
             del s2
             torch.cuda.empty_cache()
 
+    if not args.no_variants and args.workload == "c2" and args.prec is None:
+        # the batched sweep: 64 uneven lattices with wires, FP16 shifted storage, one launch per step
+        w4 = workloads.batched_c4("fp16")
+        s4 = make_sim(w4)
+        s4.step(args.warmup)
+        if not args.no_autotune:
+            s4.autotune(2)
+            s4.step(2)
+        s4.sync()
+        k4 = max(20, args.steps // 4)
+        m4 = barrier_max(time_steps(s4, k4))
+        mlups4 = world * w4.nodes * k4 / (m4 * 1e-3) / 1e6
+        variants["fp16_batched_c4"] = {"value": round(mlups4, 1), "unit": "MLUPS",
+                                       "speedup_vs_fp32": round(mlups4 / value, 3),
+                                       "instances": len(w4.cfgs), "nodes": w4.nodes,
+                                       "beads": int(sum(s4.nb)), "ms_per_step": round(m4 / k4, 5)}
+        s4.close()
+        del s4
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)

@@ -196,6 +196,30 @@ lbm_status lbm_destroy(lbm_handle* h);
 
 const char* lbm_status_string(lbm_status s);
 
+/* ---------------------------------------------------------------------------
+ * Sweep proposer: a small multilayer perceptron trained on deposit
+ * descriptors of batched runs (no paper counterpart; the paper sweeps its
+ * parameters by enumeration, Sec. III).  Network: x[n_in] -> tanh(W1 x + b1)
+ * -> tanh(W2 h1 + b2) -> y = W3 h2 + b3.  Parameters are one flat array
+ * [W1 (n_hidden x n_in, row-major), b1, W2 (n_hidden x n_hidden), b2,
+ *  W3 (n_out x n_hidden), b3].  Loss L = 1/(2B) sum_b sum_k (y_bk - t_bk)^2.
+ * All arrays are caller-owned DEVICE memory of dtype 0 (float) or 1 (double),
+ * row-major [batch][n_in] / [batch][n_out]; calls are asynchronous on
+ * `stream` (a cudaStream_t).  Limits: n_in, n_out <= 16, n_hidden <= 256.
+ * ------------------------------------------------------------------------- */
+size_t lbm_mlp_param_count(int n_in, int n_hidden, int n_out);
+/* Device scratch that lbm_mlp_loss_grad() needs for activations and deltas. */
+size_t lbm_mlp_scratch_bytes(int dtype, int n_hidden, int batch);
+lbm_status lbm_mlp_forward(int dtype, const void* params, int n_in, int n_hidden, int n_out,
+                           const void* x, int batch, void* y, void* stream);
+/* Forward pass into y, loss into *loss (device scalar, may be NULL) and dL/dparams into grad. */
+lbm_status lbm_mlp_loss_grad(int dtype, const void* params, int n_in, int n_hidden, int n_out,
+                             const void* x, const void* targets, int batch, void* y, void* grad,
+                             void* loss, void* scratch, size_t scratch_bytes, void* stream);
+/* One Adam update with bias correction; `step` counts from 1. */
+lbm_status lbm_mlp_adam(int dtype, void* params, const void* grad, void* m, void* v, int n_params,
+                        double lr, double beta1, double beta2, double eps, int step, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

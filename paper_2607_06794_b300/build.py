@@ -24,7 +24,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(p) for p in sources())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    cmd = ["nvcc"] + NVCC_FLAGS + ["-o", LIB, os.path.join(SRC, "lbm_api.cu")]
+    units = [os.path.join(SRC, f) for f in sorted(os.listdir(SRC)) if f.endswith(".cu")]
+    cmd = ["nvcc"] + NVCC_FLAGS + ["-o", LIB] + units
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)

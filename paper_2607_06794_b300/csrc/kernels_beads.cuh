@@ -9,32 +9,35 @@
 
 namespace lbm {
 
-__device__ __forceinline__ double min_image(double d, int L) { return d - L * floor(d / L + 0.5); }
+// minimum image of a separation of two wrapped coordinates (|d| <= L)
+__device__ __forceinline__ double min_image(double d, int L) {
+    const double h = 0.5 * L;
+    return d > h ? d - L : (d < -h ? d + L : d);
+}
 
 // (d0/r)^12 - 2 (d0/r)^6 and its r-derivative (Eq. (12) without prefactor)
-__device__ __forceinline__ double lj_shape(double d0, double r) {
-    const double s = d0 / r, s2 = s * s, s6 = s2 * s2 * s2;
-    return s6 * s6 - 2.0 * s6;
-}
-__device__ __forceinline__ double lj_shape_dr(double d0, double r) {
-    const double s = d0 / r, s2 = s * s, s6 = s2 * s2 * s2;
-    return (-12.0 * s6 * s6 + 12.0 * s6) / r;
+template <typename T>
+__device__ __forceinline__ T lj_shape_dr(T d0, T r) {
+    const T s = d0 / r, s2 = s * s, s6 = s2 * s2 * s2;
+    return (T(-12) * s6 * s6 + T(12) * s6) / r;
 }
 
 // dU/dr of a bead pair; `sep` = |index difference| if same filament, else 0
-__device__ __forceinline__ double pair_dUdr(const InstDev& I, bool same, int sep, double r, int& err) {
-    double f = 0.0;
+template <typename T>
+__device__ __forceinline__ T pair_dUdr(const InstDev& I, bool same, int sep, T r, int& err) {
+    T f = 0;
+    const T d0 = (T)I.d0;
     if (same && sep == 1) {  // FENE, Eq. (9)
-        double q = r * r / (I.Rm * I.Rm);
-        if (q >= 1.0) {
+        T q = r * r / (T)(I.Rm * I.Rm);
+        if (q >= T(1)) {
             err |= ERR_FENE;
-            q = 0.99;
+            q = T(0.99);
         }
-        f += I.ks * r / (1.0 - q);
+        f += (T)I.ks * r / (T(1) - q);
     }
-    if (same && sep == 2) f += I.kb * (r - 2.0 * I.d0);  // bending, Eq. (11)
-    if (r <= I.d0) f += I.eps_wca * lj_shape_dr(I.d0, r);  // WCA, Eq. (10)
-    if (!same && I.eps_coh > 0.0 && r > I.d0 && r < I.rc) f += I.eps_coh * lj_shape_dr(I.d0, r);
+    if (same && sep == 2) f += (T)I.kb * (r - T(2) * d0);  // bending, Eq. (11)
+    if (r <= d0) f += (T)I.eps_wca * lj_shape_dr<T>(d0, r);  // WCA, Eq. (10)
+    if (!same && I.eps_coh > 0.0 && r > d0 && r < (T)I.rc) f += (T)I.eps_coh * lj_shape_dr<T>(d0, r);
     return f;
 }
 
@@ -240,30 +243,40 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
 }
 
 // Verlet neighbour list for the step: pairs closer than rlist that are not
-// bonded or bending partners (those are handled by index).
+// bonded or bending partners (those are handled by index).  One warp per
+// bead; lanes stride over the other beads and the list stays in index order.
 __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
     const InstDev I = insts[blockIdx.y];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= I.nb) return;
     const double xa = I.bx[3 * a], ya = I.bx[3 * a + 1], za = I.bx[3 * a + 2];
     const int fa = I.bfil[a], pa = I.bpos[a];
-    const double r2 = I.rlist * I.rlist;
+    const float r2 = (float)(I.rlist * I.rlist);
     int cnt = 0;
-    for (int b = 0; b < I.nb; ++b) {
-        if (b == a) continue;
-        if (I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2) continue;
-        const double dx = min_image(I.bx[3 * b] - xa, I.nx), dy = min_image(I.bx[3 * b + 1] - ya, I.ny),
-                     dz = I.bx[3 * b + 2] - za;
-        if (dx * dx + dy * dy + dz * dz < r2) {
-            if (cnt < I.max_nbr) I.nbr[(long long)a * I.max_nbr + cnt] = b;
-            ++cnt;
+    for (int b0 = 0; b0 < I.nb; b0 += 32) {
+        const int b = b0 + lane;
+        bool hit = false;
+        if (b < I.nb && b != a && !(I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2)) {
+            const float dx = (float)min_image(I.bx[3 * b] - xa, I.nx);
+            const float dy = (float)min_image(I.bx[3 * b + 1] - ya, I.ny);
+            const float dz = (float)(I.bx[3 * b + 2] - za);
+            hit = dx * dx + dy * dy + dz * dz < r2;
         }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int k = cnt + __popc(m & ((1u << lane) - 1u));
+            if (k < I.max_nbr) I.nbr[(long long)a * I.max_nbr + k] = b;
+        }
+        cnt += __popc(m);
     }
-    if (cnt > I.max_nbr) {
-        atomicOr(I.err, ERR_CAP);
-        cnt = I.max_nbr;
+    if (lane == 0) {
+        if (cnt > I.max_nbr) {
+            atomicOr(I.err, ERR_CAP);
+            cnt = I.max_nbr;
+        }
+        I.nnbr[a] = cnt;
     }
-    I.nnbr[a] = cnt;
 }
 
 // First half kick and drift of the step
@@ -300,14 +313,18 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     const double P[3] = {cur[3 * a], cur[3 * a + 1], cur[3 * a + 2]};
     const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     const int fa = I.bfil[a], pa = I.bpos[a];
+    // pair forces in the compute type (FP32 outside the FP64 validation path),
+    // summed in FP64 like the integration
     double f[3] = {0.0, 0.0, 0.0};
     auto pair = [&](int b, bool same, int sep) {
-        double d[3] = {min_image(cur[3 * b] - P[0], I.nx), min_image(cur[3 * b + 1] - P[1], I.ny),
-                       cur[3 * b + 2] - P[2]};
-        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        const double g = pair_dUdr(I, same, sep, r, err);
-        if (g != 0.0)
-            for (int k = 0; k < 3; ++k) f[k] += g * d[k] / r;
+        const T d[3] = {(T)min_image(cur[3 * b] - P[0], I.nx), (T)min_image(cur[3 * b + 1] - P[1], I.ny),
+                        (T)(cur[3 * b + 2] - P[2])};
+        const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const T g = pair_dUdr<T>(I, same, sep, r, err);
+        if (g != T(0)) {
+            const T gr = g / r;
+            for (int k = 0; k < 3; ++k) f[k] += (double)(gr * d[k]);
+        }
     };
     for (int k = -2; k <= 2; ++k) {
         const int b = a + k;
@@ -340,7 +357,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     // substrate adhesion (LJ at the image distance) and load-dependent friction
     const double rw = 2.0 * (P[2] + 0.5);
     double fw = 0.0;
-    if (I.eps_s > 0.0 && rw < I.rc && rw > 0.0) fw = -2.0 * I.eps_s * lj_shape_dr(I.d0, rw);
+    if (I.eps_s > 0.0 && rw < I.rc && rw > 0.0) fw = -2.0 * I.eps_s * lj_shape_dr<double>(I.d0, rw);
     if (I.eps_s > 0.0 && rw < I.rc) {
         const double load = (f[2] < 0.0 ? -f[2] : 0.0) + (fw < 0.0 ? -fw : 0.0);
         const double vt = sqrt(vh[0] * vh[0] + vh[1] * vh[1]);

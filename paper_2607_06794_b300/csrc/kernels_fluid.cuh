@@ -58,8 +58,11 @@ __device__ T colour_ext(const InstDev& I, const T* __restrict__ rho, int x, int 
 // halo into which every stored population is pushed to the node it streams
 // to next step.  Fully interior nodes are stored plainly; tile-edge and halo
 // nodes are added atomically (their buffer was zeroed one step earlier).
-// Per plane: [pull loads of plane z; flush plane z-2; C of plane z+2] |
-// [normals of plane z+1] | [collide plane z, store, push].
+// Per plane z, separated by barriers:
+//   1. issue the 38 pull loads of plane z (consumed in 3), flush plane z-2,
+//      store the prefetched C of plane z+2, prefetch C of plane z+3
+//   2. gradient and normals of plane z+1
+//   3. decode the pulled pairs, collide, recolour, evaporate, store, push
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int wrap_near(int a, int n) {
     while (a < 0) a += n;
@@ -74,14 +77,46 @@ __device__ __forceinline__ float inv_norm<float>(float g2) { return rsqrtf(g2); 
 template <>
 __device__ __forceinline__ double inv_norm<double>(double g2) { return 1.0 / sqrt(g2); }
 
+// Liquid column height h(x,y) = sum_z (1 + C)/2 of the current moments (Eq. (8)),
+// one thread per column, for instances whose sink is on in this step.
+template <typename T>
+__global__ void k_column_height(const InstDev* __restrict__ insts, const StepGlobals* __restrict__ glob) {
+    const InstDev& I = insts[blockIdx.y];
+    const long long step = __ldcg(&glob->step);
+    if (!(I.J0 > 0.0 && I.evap_start >= 0 && step >= I.evap_start) || I.hcol == nullptr) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned nxy = (unsigned)I.nx * I.ny;
+    if (c >= (int)nxy) return;
+    const T* __restrict__ rho = (const T*)I.rho[step % 3];
+    const unsigned N = (unsigned)I.N;
+    T h = 0;
+    int z = 0;
+    for (; z + 8 <= I.nz; z += 8) {
+        T a[8], b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a[k] = rho[(unsigned)(z + k) * nxy + c];
+            b[k] = rho[N + (unsigned)(z + k) * nxy + c];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h += (T(1) + (a[k] - b[k]) / (a[k] + b[k])) / T(2);
+    }
+    for (; z < I.nz; ++z) {
+        const T a = rho[(unsigned)z * nxy + c], b = rho[N + (unsigned)z * nxy + c];
+        h += (T(1) + (a - b) / (a + b)) / T(2);
+    }
+    ((T*)I.hcol)[c] = h;
+}
+
 template <class S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * TY)) : 1)
     k_stream_collide(const InstDev* __restrict__ insts, const TileDesc* __restrict__ tiles,
                      StepGlobals* __restrict__ glob) {
     using T = typename S::T;
     using E = typename S::E;
     constexpr int NT = TX * TY;
     constexpr int HX2 = TX + 4, HY2 = TY + 4, HX1 = TX + 2, HY1 = TY + 2;
+    constexpr int NPF = (HX2 * HY2 + NT - 1) / NT;  // C-halo slots per thread
     __shared__ T sC[3][HY2][HX2];
     __shared__ T sN[3][HY1][HX1][3];
     __shared__ T sG[2][TY][TX][3];
@@ -106,6 +141,7 @@ __global__ void __launch_bounds__(TX * TY)
     const T* __restrict__ fext = (const T*)Ig.fext;
     const unsigned* __restrict__ tflag = Ig.tflag;
     const double* __restrict__ cotm = Ig.cot;
+    const T* __restrict__ hcolm = (const T*)Ig.hcol;
     double* accp = Ig.acc;
     int* errp = Ig.err;
     const int t8x = Ig.t8x, t8y = Ig.t8y;
@@ -149,25 +185,12 @@ __global__ void __launch_bounds__(TX * TY)
         return g > T(1) ? T(1) : (g < T(-1) ? T(-1) : g);
     };
 
-    // liquid column height of this thread's column, h = sum_z (1+C)/2 (Eq. (8))
-    T hcol = 0;
-    if (evap_on && active) {
-        const unsigned c0 = (unsigned)y * nx + x;
-        int z = 0;
-        for (; z + 4 <= nz; z += 4) {
-            T c[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) c[k] = colour(c0 + (unsigned)(z + k) * nxy);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) hcol += (T(1) + c[k]) / T(2);
-        }
-        for (; z < nz; ++z) hcol += (T(1) + colour(c0 + (unsigned)z * nxy)) / T(2);
-    }
+    const T hcol = (evap_on && active) ? hcolm[y * nx + x] : T(0);
 
     for (int s = tid; s < 3 * HY1 * HX1 * 2; s += NT) (&sA[0][0][0][0])[s] = T(0);
     if (tid == 0) sErr = 0;
 
-    // C of plane p into the ring over the tile plus 2 cells
+    // C of plane p into the ring over the tile plus 2 cells (synchronous form)
     auto loadC = [&](int p) {
         if (p < -1 || p > nz) return;
         const int r = ring(p);
@@ -177,6 +200,38 @@ __global__ void __launch_bounds__(TX * TY)
             if (sx > tw + 3 || sy > th + 3) continue;
             const int gx = wrap_near(x0 - 2 + sx, nx), gy = wrap_near(y0 - 2 + sy, ny);
             sC[r][sy][sx] = p < 0 ? ghost(gx, gy) : colour((unsigned)pz * nxy + (unsigned)gy * nx + gx);
+        }
+    };
+    // prefetched form for planes p >= 0: raw moments into registers now, colour into the ring later
+    T pfa[NPF], pfb[NPF];
+    int pfp = -100;
+    auto prefetchC = [&](int p) {
+        pfp = p;
+        if (p < 0 || p > nz) return;
+        const int pz = p >= nz ? nz - 1 : p;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int s = tid + k * NT;
+            const int sy = s / HX2, sx = s - sy * HX2;
+            pfa[k] = T(1);
+            pfb[k] = T(0);
+            if (s < HX2 * HY2 && sx <= tw + 3 && sy <= th + 3) {
+                const int gx = wrap_near(x0 - 2 + sx, nx), gy = wrap_near(y0 - 2 + sy, ny);
+                const unsigned n = (unsigned)pz * nxy + (unsigned)gy * nx + gx;
+                pfa[k] = rho_r[n];
+                pfb[k] = rho_r[N + n];
+            }
+        }
+    };
+    auto commitC = [&]() {
+        if (pfp < 0 || pfp > nz) return;
+        const int r = ring(pfp);
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int s = tid + k * NT;
+            const int sy = s / HX2, sx = s - sy * HX2;
+            if (s < HX2 * HY2 && sx <= tw + 3 && sy <= th + 3)
+                sC[r][sy][sx] = (pfa[k] - pfb[k]) / (pfa[k] + pfb[k]);
         }
     };
     // gradient and unit normal of plane q over the tile plus 1 cell
@@ -282,28 +337,58 @@ __global__ void __launch_bounds__(TX * TY)
         __syncthreads();
         computeN(z0);
     }
+    prefetchC(z0 + 2);
     __syncthreads();
 
     for (int z = z0; z < z1; ++z) {
-        // ---- phase 1: pull loads of plane z (consumed in phase 3), flush, next C ----
-        T Fi[19];
-        T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
         const unsigned node = (unsigned)z * nxy + row0 + x;
+        // ---- phase 1: raw pull loads of plane z, flush, C ring upkeep ----
+        E rawR[19], rawB[19];
         if (active) {
 #pragma unroll
             for (int i = 0; i < 19; ++i) {
                 const int sz = z - cz(i);
-                T r, b;
+                unsigned k;
                 if (sz < 0 || (sz >= nz && top_bc == 0)) {
-                    S::load(src, cs, (unsigned)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
+                    k = (unsigned)opp(i) * N + node;  // half-way bounce-back
                 } else if (sz >= nz) {
+                    k = (unsigned)i * N + node;  // replaced by the gas inflow below
+                } else {
+                    const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
+                    const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
+                    k = (unsigned)i * N + (unsigned)sz * nxy + row + sx;
+                }
+                rawR[i] = __ldg(src + k);
+                rawB[i] = __ldg(src + cs + k);
+            }
+        }
+        flush(z - 2);
+        commitC();
+        prefetchC(z + 3);
+        __syncthreads();
+        // ---- phase 2: normals of plane z+1 ----
+        computeN(z + 1);
+        __syncthreads();
+        // ---- phase 3: decode, collide, recolour, evaporate, store, push ----
+        if (active) {
+            T Fi[19];
+            T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+            const bool top_gas = z == nz - 1 && top_bc == 1;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                T r, b;
+                const bool bb = (z - cz(i) < 0) || (z - cz(i) >= nz && top_bc == 0);
+                if (top_gas && cz(i) < 0) {
+                    // pure-gas equilibrium streams in; what streamed out is booked
+                    T ro, bo;
+                    S::decode(rawR[i], rawB[i], (T)wq(i), rho0, ro, bo);
+                    (void)ro;
+                    (void)bo;
                     r = T(0);
                     b = (T)wq(i) * rho0;
                     top_in += (double)b;
                 } else {
-                    const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
-                    const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
-                    S::load(src, cs, (unsigned)i * N + (unsigned)sz * nxy + row + sx, (T)wq(i), rho0, r, b);
+                    S::decode(rawR[i], rawB[i], (T)wq(bb ? opp(i) : i), rho0, r, b);
                 }
                 rR += r;
                 rB += b;
@@ -312,8 +397,7 @@ __global__ void __launch_bounds__(TX * TY)
                 if (cy(i)) jy += cy(i) * Fi[i];
                 if (cz(i)) jz += cz(i) * Fi[i];
             }
-            if (z == nz - 1 && top_bc == 1) {
-                // what left the domain through the top in this stream
+            if (top_gas) {
 #pragma unroll
                 for (int i = 0; i < 19; ++i)
                     if (cz(i) > 0) {
@@ -322,15 +406,6 @@ __global__ void __launch_bounds__(TX * TY)
                         top_out += (double)r + (double)b;
                     }
             }
-        }
-        flush(z - 2);
-        loadC(z + 2);
-        __syncthreads();
-        // ---- phase 2: normals of plane z+1 ----
-        computeN(z + 1);
-        __syncthreads();
-        // ---- phase 3: collide, recolour, evaporate, store, push ----
-        if (active) {
             T kap = 0;
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
@@ -372,16 +447,13 @@ __global__ void __launch_bounds__(TX * TY)
                 if (ht > T(0)) dm = J0 / (Kk + ht) * T(0.5) * gm;
             }
             const T rGx = Gx * ig, rGy = Gy * ig, rGz = Gz * ig;
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
+            const T base0 = T(1) - T(1.5) * usq;
+            auto emit = [&](int i, T post) {
                 const T w = (T)wq(i);
-                T cu = 0, cF = 0, cG = 0;
-                if (cx(i)) { cu += cx(i) * ux; cF += cx(i) * Fx; cG += cx(i) * rGx; }
-                if (cy(i)) { cu += cy(i) * uy; cF += cy(i) * Fy; cG += cy(i) * rGy; }
-                if (cz(i)) { cu += cz(i) * uz; cF += cz(i) * Fz; cG += cz(i) * rGz; }
-                const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
-                const T Sg = gsrc * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-                const T post = Fi[i] - omega * (Fi[i] - feq) + Sg;
+                T cG = 0;
+                if (cx(i)) cG += cx(i) * rGx;
+                if (cy(i)) cG += cy(i) * rGy;
+                if (cz(i)) cG += cz(i) * rGz;
                 T r = phi * post + coef * w * (cG * (T)inv_len(i));
                 T b = post - r;
                 if (i == 0 && evap_on) {
@@ -405,8 +477,30 @@ __global__ void __launch_bounds__(TX * TY)
                     atomicAdd(a, rq);
                     atomicAdd(a + 1, bq);
                 }
+            };
+            {  // rest direction
+                const T w = (T)wq(0);
+                const T feq = w * rho * base0;
+                const T Sg = gsrc * w * (T(-3) * uF);
+                emit(0, Fi[0] - omega * (Fi[0] - feq) + Sg);
             }
-            if (z == nz - 1 && top_bc == 1) {
+#pragma unroll
+            for (int i = 1; i < 19; i += 2) {
+                // the pair (i, opp(i) = i+1) shares c.u, c.F and c.G up to sign
+                const T w = (T)wq(i);
+                T cu = 0, cF = 0;
+                if (cx(i)) { cu += cx(i) * ux; cF += cx(i) * Fx; }
+                if (cy(i)) { cu += cy(i) * uy; cF += cy(i) * Fy; }
+                if (cz(i)) { cu += cz(i) * uz; cF += cz(i) * Fz; }
+                const T wr = w * rho;
+                const T even = wr * (base0 + T(4.5) * cu * cu);
+                const T odd = wr * (T(3) * cu);
+                const T se = gsrc * w * (T(9) * cu * cF - T(3) * uF);
+                const T so = gsrc * w * (T(3) * cF);
+                emit(i, Fi[i] - omega * (Fi[i] - (even + odd)) + (se + so));
+                emit(i + 1, Fi[i + 1] - omega * (Fi[i + 1] - (even - odd)) + (se - so));
+            }
+            if (top_gas) {
                 // gas inflow that the next stream brings to this node
                 T inB = 0;
 #pragma unroll

@@ -104,6 +104,7 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
         for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb);
         for (int p = 0; p < 3; ++p) I.rho[p] = cv.take(2 * I.N * cb);
         I.cot = (double*)cv.take(sizeof(double) * c.nx * c.ny);
+        I.hcol = cv.take(cb * c.nx * c.ny);
         I.acc = (double*)cv.take(sizeof(double) * 8);
         I.err = (int*)cv.take(sizeof(int));
         I.desc = (double*)cv.take(sizeof(double) * 8);
@@ -237,13 +238,13 @@ lbm_status launch_beads(lbm_handle* h) {
             CK(cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int),
                                h->stream));
     }
-    const int bt = 128;
+    const int bt = 64;  // small blocks spread the few hundred beads over many SMs
     const dim3 gb((h->max_nb + bt - 1) / bt, n);
     k_bead_begin<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
     int maxt = 0;
     for (auto& I : h->L.inst) maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
     k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
-    k_bead_nlist<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
+    k_bead_nlist<<<dim3((h->max_nb * 32 + 255) / 256, n), 256, 0, h->stream>>>(h->L.d_inst);
     k_bead_kickdrift<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
     const int S_ = h->cfg[0].substeps;
     for (int s = 1; s <= S_; ++s) k_bead_force<T><<<gb, bt, 0, h->stream>>>(h->L.d_inst, s);
@@ -252,8 +253,25 @@ lbm_status launch_beads(lbm_handle* h) {
 }
 
 template <class S>
+lbm_status launch_heights(lbm_handle* h) {
+    using T = typename S::T;
+    int maxc = 0;
+    bool any = false;
+    for (size_t k = 0; k < h->cfg.size(); ++k) {
+        maxc = std::max(maxc, h->cfg[k].nx * h->cfg[k].ny);
+        any |= h->cfg[k].J0 > 0 && h->cfg[k].evap_start >= 0;
+    }
+    if (!any) return LBM_OK;
+    k_column_height<T><<<dim3((maxc + 255) / 256, (unsigned)h->cfg.size()), 256, 0, h->stream>>>(h->L.d_inst,
+                                                                                             h->L.glob);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+template <class S>
 lbm_status enqueue_step(lbm_handle* h) {
     lbm_status st = launch_beads<S>(h);
+    if (st == LBM_OK) st = launch_heights<S>(h);
     if (st != LBM_OK) return st;
     return launch_fused<S>(h);
 }
@@ -487,7 +505,45 @@ lbm_status place_random(lbm_handle* h, int k, int nw, int nbf, double spacing, u
         if (z < 0 || z >= c.nz) return -1.0;
         return C[((long long)z * c.ny + y) * c.nx + x];
     };
+    // beads already placed, hashed on a grid of cell size d0 for the overlap test
+    const double cell = c.d0;
+    const int gx = std::max(1, (int)floor(c.nx / cell)), gy = std::max(1, (int)floor(c.ny / cell)),
+              gz = std::max(1, (int)ceil((c.nz + 1.0) / cell));
+    std::vector<std::vector<int>> grid((size_t)gx * gy * gz);
     std::vector<double> placed = have;
+    auto cell_of = [&](const double* P, int& ix, int& iy, int& iz) {
+        ix = std::min(gx - 1, std::max(0, (int)floor(P[0] / cell)));
+        iy = std::min(gy - 1, std::max(0, (int)floor(P[1] / cell)));
+        iz = std::min(gz - 1, std::max(0, (int)floor((P[2] + 1.0) / cell)));
+    };
+    auto add = [&](int q) {
+        int ix, iy, iz;
+        cell_of(&placed[3 * q], ix, iy, iz);
+        grid[((size_t)iz * gy + iy) * gx + ix].push_back(q);
+    };
+    for (size_t q = 0; q < placed.size() / 3; ++q) add((int)q);
+    auto clash = [&](const double* P) {
+        int ix, iy, iz;
+        cell_of(P, ix, iy, iz);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int zz = iz + dz;
+                    if (zz < 0 || zz >= gz) continue;
+                    const int xx = ((ix + dx) % gx + gx) % gx, yy = ((iy + dy) % gy + gy) % gy;
+                    for (int q : grid[((size_t)zz * gy + yy) * gx + xx]) {
+                        double dd = 0;
+                        for (int d = 0; d < 3; ++d) {
+                            double e = P[d] - placed[3 * q + d];
+                            if (d == 0) e -= c.nx * floor(e / c.nx + 0.5);
+                            if (d == 1) e -= c.ny * floor(e / c.ny + 0.5);
+                            dd += e * e;
+                        }
+                        if (dd <= c.d0 * c.d0) return true;
+                    }
+                }
+        return false;
+    };
     const long long max_tries = 200000LL + 2000LL * nw;
     long long tries = 0;
     int got = 0;
@@ -507,26 +563,17 @@ lbm_status place_random(lbm_handle* h, int k, int nw, int nbf, double spacing, u
         bool ok = true;
         for (int b = 0; b < nbf && ok; ++b) {
             for (int d = 0; d < 3; ++d) cand[3 * b + d] = cen[d] + (b - (nbf - 1) / 2.0) * spacing * dir[d];
-            if (cand[3 * b + 2] < 1.0 || cand[3 * b + 2] > c.nz - 2.0) ok = false;
-            if (ok && colour_at(&cand[3 * b]) <= 0.9) ok = false;
-        }
-        for (size_t q = 0; q < placed.size() / 3 && ok; ++q)
-            for (int b = 0; b < nbf && ok; ++b) {
-                double dd = 0;
-                for (int d = 0; d < 3; ++d) {
-                    double e = cand[3 * b + d] - placed[3 * q + d];
-                    if (d == 0) e -= c.nx * floor(e / c.nx + 0.5);
-                    if (d == 1) e -= c.ny * floor(e / c.ny + 0.5);
-                    dd += e * e;
-                }
-                if (dd <= c.d0 * c.d0) ok = false;
-            }
-        if (!ok) continue;
-        for (int b = 0; b < nbf; ++b) {
             cand[3 * b] -= c.nx * floor(cand[3 * b] / c.nx);
             cand[3 * b + 1] -= c.ny * floor(cand[3 * b + 1] / c.ny);
+            if (cand[3 * b + 2] < 1.0 || cand[3 * b + 2] > c.nz - 2.0) ok = false;
+            if (ok && colour_at(&cand[3 * b]) <= 0.9) ok = false;
+            if (ok && clash(&cand[3 * b])) ok = false;
         }
-        placed.insert(placed.end(), cand.begin(), cand.end());
+        if (!ok) continue;
+        for (int b = 0; b < nbf; ++b) {
+            placed.insert(placed.end(), &cand[3 * b], &cand[3 * b] + 3);
+            add((int)(placed.size() / 3 - 1));
+        }
         X.insert(X.end(), cand.begin(), cand.end());
         ++got;
     }
@@ -765,6 +812,13 @@ lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, doubl
             case LBM_FP32: st = launch_beads<StoreF32>(h); break;
             case LBM_FP16_SHIFTED: st = launch_beads<StoreF16>(h); break;
             default: st = launch_beads<StoreB16>(h); break;
+        }
+        if (st != LBM_OK) break;
+        switch (h->prec) {
+            case LBM_FP64: st = launch_heights<StoreF64>(h); break;
+            case LBM_FP32: st = launch_heights<StoreF32>(h); break;
+            case LBM_FP16_SHIFTED: st = launch_heights<StoreF16>(h); break;
+            default: st = launch_heights<StoreB16>(h); break;
         }
         if (st != LBM_OK) break;
         cudaEventRecord(ev[3 * s + 1], h->stream);

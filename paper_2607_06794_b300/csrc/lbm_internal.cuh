@@ -48,6 +48,10 @@ enum : int { ERR_NAN = 1, ERR_FENE = 2, ERR_BEAD = 4, ERR_TIMEOUT = 8, ERR_CAP =
 struct StoreF64 {
     using T = double;
     using E = double;
+    static __device__ __forceinline__ void decode(E a, E c, T w, T rho0, T& r, T& b) {
+        r = a;
+        b = c;
+    }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         r = __ldg(p + k);
@@ -75,6 +79,10 @@ struct StoreF64 {
 struct StoreF32 {
     using T = float;
     using E = float;
+    static __device__ __forceinline__ void decode(E a, E c, T w, T rho0, T& r, T& b) {
+        r = a;
+        b = c;
+    }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         r = __ldg(p + k);
@@ -129,6 +137,9 @@ struct StoreShift16 {
         r = (psi + 0.5f) * F;
         b = F - r;
     }
+    static __device__ __forceinline__ void decode(H P, H psi, float w, float rho0, float& r, float& b) {
+        decode(Cvt<H>::f(P), Cvt<H>::f(psi), w, rho0, r, b);
+    }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         float P = Cvt<H>::f(p[k]);
@@ -174,6 +185,7 @@ struct InstDev {
     void* fext;                  // [N][3] bead force on the fluid (compute type)
     void* ust;                   // [N][3] u* near beads (compute type)
     void* gcol;                  // [N][3] grad C near beads (compute type)
+    void* hcol;                  // [ny][nx] liquid column height of the step (compute type)
     unsigned* tflag;             // [t8z][t8y][t8x] coupling-tile flags
     int* tlist;                  // flagged tiles of this step (compact)
     int* tcount;                 // number of entries in tlist

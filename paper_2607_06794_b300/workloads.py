@@ -67,8 +67,8 @@ def droplet_c2(prec="fp32", wires=200):
 
 
 def droplet_c5(prec="fp16", wires=2000):
-    """512x256x128, aspect-6 cap 192x32x32 on periodic stripes (64/32), 2000 wires L=16."""
-    c = Config(512, 256, 128, prec=prec, cx=255.5, cy=127.5, cz=-0.5, a=192, b=32, c=32,
+    """512x256x128, aspect-6 cap 192x32x48 on periodic stripes (64/32), 2000 wires L=16."""
+    c = Config(512, 256, 128, prec=prec, cx=255.5, cy=127.5, cz=-0.5, a=192, b=32, c=48,
                width=2.0, theta_deg=110.0, J0=2e-4, evap_start=0, top_bc=1,
                max_beads=8 * wires + 64, eps_coh=0.006, xi=0.05, gamma=1.0,
                x_src=255.5 - 0.26 * 384, x_snk=255.5 + 0.26 * 384, seed=4321)
@@ -99,7 +99,6 @@ def batched_c4(prec="fp16", n=64):
                 b = 12.0
                 a = b * ar
                 nx = int(min(192, max(64, 32 * np.ceil((2 * a + 24) / 32))))
-                ny = 64 if ar > 1.5 else 64
                 ny = int(min(96, max(64, 32 * np.ceil((2 * b + 40) / 32))))
                 nz = 48
                 vol = 2.0 / 3.0 * np.pi * a * b * 14.0

@@ -1,0 +1,61 @@
+"""Learned sweep proposer: what it gains over plain enumeration, and the
+end-to-end loop on real batched lattice runs."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2607_06794_b300 import build
+    build.build()
+    from paper_2607_06794_b300 import sweep as S
+    return S
+
+
+def smooth_response(P):
+    """A smooth stand-in for the descriptors (S_x, clusters, percolation) whose best
+    point lies in the middle of the grid, far from where enumeration starts."""
+    ar, e, L, sw = P[:, 0], P[:, 1], P[:, 2], P[:, 3]
+    s = np.tanh(0.4 * (ar - 3.5)) * 0.5 + 0.02 * L
+    c = 1.0 / (1.0 + e) + 0.01 * sw
+    p = np.exp(-((ar - 4.0) ** 2) / 2.0 - (e - 1.0) ** 2 - ((L - 12.0) / 4.0) ** 2 - ((sw - 16.0) / 8.0) ** 2)
+    return np.c_[s, c, p]
+
+
+def test_proposer_beats_enumeration_at_equal_budget(sweep):
+    grid = sweep.default_grid()
+    objective = lambda y: float(y[2])  # maximise percolation
+    budget = 40
+    act = sweep.active_sweep(grid, smooth_response, objective, budget, seed_points=16, per_round=8,
+                             seed=3, epochs=600)
+    ref = sweep.grid_sweep(grid, smooth_response, objective, budget)
+    best_possible = smooth_response(grid)[:, 2].max()
+    assert len(act.evaluated) == budget == len(ref.evaluated)
+    assert act.best > ref.best + 0.2
+    assert act.best > 0.8 * best_possible
+    # every proposal was judged by simulation and its prediction error recorded
+    assert len(act.prediction_error) == budget - 16
+
+
+def test_proposer_fit_reduces_loss(sweep):
+    grid = sweep.default_grid()
+    Y = smooth_response(grid)
+    prop = sweep.Proposer(seed=1)
+    l0 = prop.fit(grid[:50], Y[:50], epochs=1)
+    l1 = prop.fit(grid[:50], Y[:50], epochs=800)
+    assert l1 < 0.1 * l0
+
+
+def test_sweep_loop_on_real_batched_runs(sweep):
+    pts = np.array([(1.0, 0.0, 4.0, 12.0), (3.0, 1.0, 8.0, 16.0), (2.0, 2.0, 12.0, 24.0)])
+    rows = sweep.batched_points(pts, steps=20, prec="fp16")
+    assert rows.shape == (3, 3)
+    assert np.all(np.abs(rows[:, 0]) <= 1.0)
+    res = sweep.active_sweep(pts, lambda P: sweep.batched_points(P, 10, "fp16"), lambda y: float(y[2]),
+                             budget=3, seed_points=2, per_round=1, epochs=50)
+    assert len(res.evaluated) == 3
