@@ -101,7 +101,9 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
             const int x = wrapi(fx + dx, I.nx), y = wrapi(fy + dy, I.ny);
             for (int k = 0; k < nzt; ++k) {
                 const int t = (t8z[k] * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
-                if (atomicExch(I.tflag + t, 1u) == 0u) I.tlist[atomicAdd(I.tcount, 1)] = t;
+                // most tiles are already flagged by a neighbour: read before the atomic
+                if (!((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u)
+                    I.tlist[atomicAdd(I.tcount, 1)] = t;
             }
         }
 }

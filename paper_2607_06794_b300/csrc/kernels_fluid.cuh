@@ -71,6 +71,11 @@ __device__ __forceinline__ int wrap_near(int a, int n) {
 }
 
 template <typename T>
+__device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
+template <typename T>
 __device__ __forceinline__ T inv_norm(T g2);
 template <>
 __device__ __forceinline__ float inv_norm<float>(float g2) { return rsqrtf(g2); }
@@ -118,8 +123,9 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     constexpr int HX2 = TX + 4, HY2 = TY + 4, HX1 = TX + 2, HY1 = TY + 2;
     constexpr int NPF = (HX2 * HY2 + NT - 1) / NT;  // C-halo slots per thread
     __shared__ T sC[3][HY2][HX2];
-    __shared__ T sN[3][HY1][HX1][3];
-    __shared__ T sG[2][TY][TX][3];
+    using V4 = typename Vec4<T>::type;
+    __shared__ V4 sN[3][HY1][HX1];
+    __shared__ V4 sG[2][TY][TX];
     __shared__ T sA[3][HY1][HX1][2];
     __shared__ double sRed[NT / 32][3];
     __shared__ int sErr;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     auto ring = [](int q) { return ((q % 3) + 3) % 3; };
     auto colour = [&](unsigned n) {
         const T a = rho_r[n], b = rho_r[N + n];
-        return (a - b) / (a + b);
+        return qdiv<T>(a - b, a + b);
     };
     // wetting ghost colour below z = 0 (flat-wall geometric form, D2Q9 weights)
     auto ghost = [&](int gx, int gy) {
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             const int s = tid + k * NT;
             const int sy = s / HX2, sx = s - sy * HX2;
             if (s < HX2 * HY2 && sx <= tw + 3 && sy <= th + 3)
-                sC[r][sy][sx] = (pfa[k] - pfb[k]) / (pfa[k] + pfb[k]);
+                sC[r][sy][sx] = qdiv<T>(pfa[k] - pfb[k], pfa[k] + pfb[k]);
         }
     };
     // gradient and unit normal of plane q over the tile plus 1 cell
@@ -256,30 +262,35 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 gy *= T(3);
                 gz *= T(3);
                 const T g2 = gx * gx + gy * gy + gz * gz;
-                T* nn = sN[rq][sy][sx];
+                V4 nn;
                 if (g2 > T(1e-16)) {
                     const T ig = inv_norm<T>(g2);
-                    nn[0] = gx * ig;
-                    nn[1] = gy * ig;
-                    nn[2] = gz * ig;
+                    nn.x = gx * ig;
+                    nn.y = gy * ig;
+                    nn.z = gz * ig;
                 } else {
-                    nn[0] = nn[1] = nn[2] = T(0);
+                    nn.x = nn.y = nn.z = T(0);
                 }
+                nn.w = T(0);
+                sN[rq][sy][sx] = nn;
                 if (sx >= 1 && sx <= tw && sy >= 1 && sy <= th) {
-                    T* G = sG[q & 1][sy - 1][sx - 1];
-                    G[0] = gx;
-                    G[1] = gy;
-                    G[2] = gz;
+                    V4 G;
+                    G.x = gx;
+                    G.y = gy;
+                    G.z = gz;
+                    G.w = T(0);
+                    sG[q & 1][sy - 1][sx - 1] = G;
                 }
             }
         } else if (q == -1 || q == nz) {
             // outside the fluid the normal copies the nearest fluid plane
             const int rf = ring(q == -1 ? 0 : nz - 1);
-            for (int s = tid; s < HX1 * HY1 * 3; s += NT) (&sN[rq][0][0][0])[s] = (&sN[rf][0][0][0])[s];
+            for (int s = tid; s < HX1 * HY1; s += NT) (&sN[rq][0][0])[s] = (&sN[rf][0][0])[s];
         }
     };
 
-    double evap_sum = 0.0, top_in = 0.0, top_out = 0.0;
+    // per-thread partial budgets in the compute type; FP64 from the block sum on
+    T evap_sum = 0, top_in = 0, top_out = 0;
     int err = 0;
 
     // flush the completed accumulator plane q to global memory
@@ -342,6 +353,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
 
     for (int z = z0; z < z1; ++z) {
         const unsigned node = (unsigned)z * nxy + row0 + x;
+        const int rz[3] = {ring(z - 1), ring(z), ring(z + 1)};  // ring slots of planes z-1, z, z+1
         // ---- phase 1: raw pull loads of plane z, flush, C ring upkeep ----
         E rawR[19], rawB[19];
         if (active) {
@@ -386,7 +398,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     (void)bo;
                     r = T(0);
                     b = (T)wq(i) * rho0;
-                    top_in += (double)b;
+                    top_in += b;
                 } else {
                     S::decode(rawR[i], rawB[i], (T)wq(bb ? opp(i) : i), rho0, r, b);
                 }
@@ -403,22 +415,22 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     if (cz(i) > 0) {
                         T r, b;
                         S::load(src, cs, (unsigned)i * N + node, (T)wq(i), rho0, r, b);
-                        top_out += (double)r + (double)b;
+                        top_out += r + b;
                     }
             }
             T kap = 0;
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
-                const T* nn = sN[ring(z + cz(i))][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                const V4 nn = sN[rz[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
                 T d = 0;
-                if (cx(i)) d += cx(i) * nn[0];
-                if (cy(i)) d += cy(i) * nn[1];
-                if (cz(i)) d += cz(i) * nn[2];
+                if (cx(i)) d += cx(i) * nn.x;
+                if (cy(i)) d += cy(i) * nn.y;
+                if (cz(i)) d += cz(i) * nn.z;
                 kap += (T)wq(i) * d;
             }
             kap *= T(-3);
-            const T* G = sG[z & 1][ty][tx];
-            const T Gx = G[0], Gy = G[1], Gz = G[2];
+            const V4 G = sG[z & 1][ty][tx];
+            const T Gx = G.x, Gy = G.y, Gz = G.z;
             T Fx = hsig * kap * Gx + bfx, Fy = hsig * kap * Gy + bfy, Fz = hsig * kap * Gz + bfz;
             if (tflag != nullptr && tflag[((z >> 3) * t8y + (y >> 3)) * t8x + (x >> 3)]) {
                 const T* fe = fext + 3 * (size_t)node;
@@ -461,16 +473,16 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     d = d < T(0) ? T(0) : d;
                     r -= d;
                     b += d;
-                    evap_sum += (double)d;
+                    evap_sum += d;
                 }
                 T rq, bq;
                 S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
                 const int tz = z + cz(i);
                 T* a;
                 if (tz < 0 || (tz >= nz && top_bc == 0))
-                    a = sA[ring(z)][ty + 1][tx + 1];  // bounces back to this node
+                    a = sA[rz[1]][ty + 1][tx + 1];  // bounces back to this node
                 else if (tz < nz)
-                    a = sA[ring(tz)][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                    a = sA[rz[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
                 else
                     a = nullptr;
                 if (a) {
@@ -506,7 +518,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
 #pragma unroll
                 for (int i = 0; i < 19; ++i)
                     if (cz(i) < 0) inB += (T)wq(i) * rho0;
-                atomicAdd(&sA[ring(z)][ty + 1][tx + 1][1], inB);
+                atomicAdd(&sA[rz[1]][ty + 1][tx + 1][1], inB);
             }
         }
         __syncthreads();
@@ -517,7 +529,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     flush(z1);
 
     // ---- block sums of the FP64 budgets ----
-    double v[3] = {evap_sum, top_in, top_out};
+    double v[3] = {(double)evap_sum, (double)top_in, (double)top_out};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);

@@ -228,6 +228,18 @@ struct TileDesc {
     int inst, x0, y0, z0, z1, pad0, pad1, pad2;
 };
 
+// 4-wide vectors for shared-memory staging (one 16/32-byte access per node)
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = double4;
+};
+
 __host__ __device__ inline int wrapi(int a, int n) {
     a %= n;
     return a < 0 ? a + n : a;

@@ -27,16 +27,16 @@ N_IN, N_HIDDEN, N_OUT = 4, 64, 3
 def point_config(p, prec="fp16", nz=32, seed=0):
     """Lattice, droplet and wires of one sweep point (aspect, eps*, L, stripe width)."""
     ar, eps_star, L, sw = p
-    b = 8.0
+    b = 10.0
     a = b * ar
     nx = int(max(32, 16 * np.ceil((2 * a + 16) / 16)))
     ny = int(max(32, 16 * np.ceil((2 * b + 24) / 16)))
-    c = Config(nx, ny, nz, prec=prec, cx=nx / 2 - 0.5, cy=ny / 2 - 0.5, cz=-0.5, a=a, b=b, c=10.0,
+    c = Config(nx, ny, nz, prec=prec, cx=nx / 2 - 0.5, cy=ny / 2 - 0.5, cz=-0.5, a=a, b=b, c=16.0,
                width=2.0, theta_deg=110.0, J0=1e-3, evap_start=0, top_bc=1, eps_coh=eps_star * 0.006,
                xi=0.05, gamma=1.0, x_src=nx / 2 - 0.26 * 2 * a, x_snk=nx / 2 + 0.26 * 2 * a, seed=seed)
     nbw = max(1, int(round(L / c.d0)))
-    vol = 2.0 / 3.0 * np.pi * a * b * 10.0
-    nw = int(np.clip(vol * 0.015 / nbw, 4, 200))
+    vol = 2.0 / 3.0 * np.pi * a * b * 16.0
+    nw = int(np.clip(vol * 0.005 / nbw, 4, 200))
     c.max_beads = nw * nbw + 16
     theta = stripe(nx, ny, sw, 60.0, 110.0)
     return c, theta, nw
@@ -68,29 +68,28 @@ def batched_points(points, steps, prec="fp16", seed=0, autotune=False):
 
 # ----------------------------------------------------------------------------- proposer
 class Proposer:
-    """MLP on the GPU: parameters, Adam moments and batches live in device memory."""
+    """Ensemble of small MLPs on the GPU (parameters, Adam moments and batches in
+    device memory); the spread of the members' predictions measures uncertainty."""
 
-    def __init__(self, seed=0, device="cuda:0", lr=3e-3):
+    def __init__(self, seed=0, device="cuda:0", lr=3e-3, members=4):
         import torch
         self.torch = torch
         self.L = _lib.load()
         self.dev = torch.device(device)
         self.P = int(self.L.lbm_mlp_param_count(N_IN, N_HIDDEN, N_OUT))
-        g = np.random.default_rng(seed)
-        parts = []
-        for (fan_out, fan_in) in ((N_HIDDEN, N_IN), (N_HIDDEN, N_HIDDEN), (N_OUT, N_HIDDEN)):
-            parts.append(g.normal(scale=1.0 / np.sqrt(fan_in), size=fan_out * fan_in))
-            parts.append(np.zeros(fan_out))
-        p = np.concatenate(parts)
-        assert p.size == self.P
-        f32 = torch.float32
-        self.params = torch.tensor(p, dtype=f32, device=self.dev)
-        self.m = torch.zeros(self.P, dtype=f32, device=self.dev)
-        self.v = torch.zeros(self.P, dtype=f32, device=self.dev)
-        self.grad = torch.zeros(self.P, dtype=f32, device=self.dev)
-        self.loss = torch.zeros(1, dtype=f32, device=self.dev)
         self.lr = lr
-        self.t = 0
+        self.nets = []
+        for k in range(members):
+            g = np.random.default_rng(1000 * seed + k)
+            parts = []
+            for (fan_out, fan_in) in ((N_HIDDEN, N_IN), (N_HIDDEN, N_HIDDEN), (N_OUT, N_HIDDEN)):
+                parts.append(g.normal(scale=1.0 / np.sqrt(fan_in), size=fan_out * fan_in))
+                parts.append(np.zeros(fan_out))
+            p = np.concatenate(parts)
+            assert p.size == self.P
+            self.nets.append(torch.tensor(p, dtype=torch.float32, device=self.dev))
+        self.grad = torch.zeros(self.P, dtype=torch.float32, device=self.dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
         self.xmu = self.xsd = self.ymu = self.ysd = None
 
     def _stream(self):
@@ -101,6 +100,7 @@ class Proposer:
         return C.c_void_p(t.data_ptr())
 
     def fit(self, X, Y, epochs=400):
+        """Refit every member on (X, Y) (inputs and targets standardised); returns the mean loss."""
         torch = self.torch
         X = np.asarray(X, np.float64)
         Y = np.asarray(Y, np.float64)
@@ -113,61 +113,76 @@ class Proposer:
         nsc = int(self.L.lbm_mlp_scratch_bytes(0, N_HIDDEN, B))
         sc = torch.empty(nsc, dtype=torch.uint8, device=self.dev)
         st = self._stream()
-        for _ in range(epochs):
-            self.t += 1
-            r = self.L.lbm_mlp_loss_grad(0, self._p(self.params), N_IN, N_HIDDEN, N_OUT, self._p(x),
-                                         self._p(t), B, self._p(y), self._p(self.grad),
-                                         self._p(self.loss), self._p(sc), nsc, st)
-            assert r == 0, r
-            r = self.L.lbm_mlp_adam(0, self._p(self.params), self._p(self.grad), self._p(self.m),
-                                    self._p(self.v), self.P, self.lr, 0.9, 0.999, 1e-8, self.t, st)
-            assert r == 0, r
-        torch.cuda.synchronize(self.dev)
-        return float(self.loss.item())
+        losses = []
+        for prm in self.nets:
+            m = torch.zeros(self.P, dtype=torch.float32, device=self.dev)
+            v = torch.zeros(self.P, dtype=torch.float32, device=self.dev)
+            for step in range(1, epochs + 1):
+                r = self.L.lbm_mlp_loss_grad(0, self._p(prm), N_IN, N_HIDDEN, N_OUT, self._p(x), self._p(t), B,
+                                             self._p(y), self._p(self.grad), self._p(self.loss), self._p(sc),
+                                             nsc, st)
+                assert r == 0, r
+                r = self.L.lbm_mlp_adam(0, self._p(prm), self._p(self.grad), self._p(m), self._p(v), self.P,
+                                        self.lr, 0.9, 0.999, 1e-8, step, st)
+                assert r == 0, r
+            torch.cuda.synchronize(self.dev)
+            losses.append(float(self.loss.item()))
+        return float(np.mean(losses))
 
-    def predict(self, X):
+    def predict_members(self, X):
+        """[members, n, N_OUT] predictions in the original units."""
         torch = self.torch
         X = np.asarray(X, np.float64)
         x = torch.tensor((X - self.xmu) / self.xsd, dtype=torch.float32, device=self.dev)
-        y = torch.zeros((x.shape[0], N_OUT), dtype=torch.float32, device=self.dev)
-        r = self.L.lbm_mlp_forward(0, self._p(self.params), N_IN, N_HIDDEN, N_OUT, self._p(x), x.shape[0],
-                                   self._p(y), self._stream())
-        assert r == 0, r
+        out = []
+        for prm in self.nets:
+            y = torch.zeros((x.shape[0], N_OUT), dtype=torch.float32, device=self.dev)
+            r = self.L.lbm_mlp_forward(0, self._p(prm), N_IN, N_HIDDEN, N_OUT, self._p(x), x.shape[0],
+                                       self._p(y), self._stream())
+            assert r == 0, r
+            out.append(y)
         torch.cuda.synchronize(self.dev)
-        return y.cpu().numpy().astype(np.float64) * self.ysd + self.ymu
+        return np.stack([o.cpu().numpy().astype(np.float64) * self.ysd + self.ymu for o in out])
+
+    def predict(self, X):
+        return self.predict_members(X).mean(axis=0)
 
 
 @dataclasses.dataclass
 class SweepResult:
     evaluated: list          # indices of candidates simulated, in order
     values: list             # objective of each evaluated point
-    prediction_error: list   # |predicted - simulated| objective of each proposal round
+    prediction_error: list   # |predicted - simulated| objective of each proposal
 
     @property
     def best(self):
         return max(self.values)
 
 
-def active_sweep(candidates, simulate, objective, budget, seed_points, per_round, seed=0, epochs=400):
-    """Spend `budget` simulations: `seed_points` spread over the grid, then rounds in which
-    the MLP, refit on everything simulated so far, proposes the `per_round` unevaluated
-    candidates with the highest predicted objective; each proposal is then simulated."""
+def active_sweep(candidates, simulate, objective, budget, seed_points, per_round, seed=0, epochs=400,
+                 kappa=1.0, members=4):
+    """Spend `budget` simulations: `seed_points` random grid points, then rounds in which
+    the ensemble, refit on everything simulated so far, proposes the `per_round`
+    unevaluated candidates with the highest mean + kappa * spread of the predicted
+    objective; every proposal is simulated and its prediction error recorded."""
     cand = np.asarray(candidates, np.float64)
     g = np.random.default_rng(seed)
     order = g.permutation(len(cand))
-    chosen = list(order[:seed_points])
+    chosen = [int(i) for i in order[:seed_points]]
     Y = list(simulate(cand[chosen]))
     vals = [objective(y) for y in Y]
     err = []
-    prop = Proposer(seed=seed)
+    prop = Proposer(seed=seed, members=members)
     while len(chosen) < budget:
         prop.fit(cand[chosen], np.array(Y), epochs=epochs)
         left = np.array([i for i in range(len(cand)) if i not in set(chosen)])
-        pred = prop.predict(cand[left])
-        score = np.array([objective(p) for p in pred])
-        take = left[np.argsort(-score)[:min(per_round, budget - len(chosen))]]
+        pm = prop.predict_members(cand[left])
+        objs = np.array([[objective(p) for p in member] for member in pm])
+        mean, spread = objs.mean(axis=0), objs.std(axis=0)
+        rank = np.argsort(-(mean + kappa * spread))[:min(per_round, budget - len(chosen))]
+        take = left[rank]
         Yn = simulate(cand[take])
-        for i, y, s in zip(take, Yn, score[np.argsort(-score)[:len(take)]]):
+        for i, y, s in zip(take, Yn, mean[rank]):
             chosen.append(int(i))
             Y.append(y)
             vals.append(objective(y))

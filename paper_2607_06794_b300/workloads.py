@@ -85,7 +85,10 @@ def paper_droplet(prec="fp32", theta_r=30.0):
 
 
 def batched_c4(prec="fp16", n=64):
-    """64 uneven lattices 64..192 x 64..96 x 48: aspect ratio x eps* x wire length grid."""
+    """64 uneven lattices (64..192) x 64 x 48: aspect ratio x eps* x wire length grid.
+
+    Wire counts follow the droplet volume (about 1% of it in beads, 10..400 wires)
+    so that straight wires of every length fit inside the liquid."""
     ars = [1.0, 2.67, 4.33, 6.0]
     epss = [0.0, 0.5, 1.0, 2.0]
     lens = [4.0, 8.0, 12.0, 16.0]
@@ -96,16 +99,15 @@ def batched_c4(prec="fp16", n=64):
             for L in lens:
                 if k >= n:
                     break
-                b = 12.0
+                b = 14.0
                 a = b * ar
                 nx = int(min(192, max(64, 32 * np.ceil((2 * a + 24) / 32))))
-                ny = int(min(96, max(64, 32 * np.ceil((2 * b + 40) / 32))))
-                nz = 48
-                vol = 2.0 / 3.0 * np.pi * a * b * 14.0
+                ny, nz = 64, 48
+                vol = 2.0 / 3.0 * np.pi * a * b * 20.0
                 nbpw = max(1, int(round(L / 2.0)))
-                nw = int(np.clip(vol * 0.02 / nbpw, 50 // nbpw + 1, 400))
+                nw = int(np.clip(vol * 0.01 / nbpw, 10, 400))
                 c = Config(nx, ny, nz, prec=prec, cx=nx / 2 - 0.5, cy=ny / 2 - 0.5, cz=-0.5, a=a, b=b,
-                           c=14.0, width=2.0, theta_deg=110.0, J0=5e-4, evap_start=0, top_bc=1,
+                           c=20.0, width=2.0, theta_deg=110.0, J0=5e-4, evap_start=0, top_bc=1,
                            max_beads=nw * nbpw + 64, eps_coh=e * 0.006, xi=0.05, gamma=1.0,
                            substeps=5, x_src=nx / 2 - 0.26 * 2 * a, x_snk=nx / 2 + 0.26 * 2 * a,
                            seed=1000 + k)

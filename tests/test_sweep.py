@@ -28,24 +28,32 @@ def smooth_response(P):
 
 
 def test_proposer_beats_enumeration_at_equal_budget(sweep):
+    """With 40 of 288 points simulated, the learned proposer finds far better points
+    than enumerating the grid in order (the fallback) and, on average over seeds,
+    better than drawing the 40 points at random."""
     grid = sweep.default_grid()
     objective = lambda y: float(y[2])  # maximise percolation
     budget = 40
-    act = sweep.active_sweep(grid, smooth_response, objective, budget, seed_points=16, per_round=8,
-                             seed=3, epochs=600)
+    truth = smooth_response(grid)[:, 2]
     ref = sweep.grid_sweep(grid, smooth_response, objective, budget)
-    best_possible = smooth_response(grid)[:, 2].max()
-    assert len(act.evaluated) == budget == len(ref.evaluated)
-    assert act.best > ref.best + 0.2
-    assert act.best > 0.8 * best_possible
-    # every proposal was judged by simulation and its prediction error recorded
-    assert len(act.prediction_error) == budget - 16
+    bests = []
+    for seed in (0, 1, 2):
+        act = sweep.active_sweep(grid, smooth_response, objective, budget, seed_points=16, per_round=8,
+                                 seed=seed, epochs=500)
+        assert len(act.evaluated) == budget == len(set(act.evaluated))
+        assert len(act.prediction_error) == budget - 16  # every proposal simulated and scored
+        bests.append(act.best)
+    g = np.random.default_rng(7)
+    random_best = np.mean([truth[g.permutation(len(grid))[:budget]].max() for _ in range(2000)])
+    assert min(bests) > ref.best + 0.3
+    assert np.mean(bests) > random_best + 0.1
+    assert max(bests) == truth.max()
 
 
 def test_proposer_fit_reduces_loss(sweep):
     grid = sweep.default_grid()
     Y = smooth_response(grid)
-    prop = sweep.Proposer(seed=1)
+    prop = sweep.Proposer(seed=1, members=1)
     l0 = prop.fit(grid[:50], Y[:50], epochs=1)
     l1 = prop.fit(grid[:50], Y[:50], epochs=800)
     assert l1 < 0.1 * l0
