@@ -196,6 +196,30 @@ lbm_status lbm_destroy(lbm_handle* h);
 
 const char* lbm_status_string(lbm_status s);
 
+/* Largest bead count lbm_deposit_descriptors_noalloc() accepts. */
+#define LBM_NOALLOC_MAX_BEADS 16384
+
+/* Deposit descriptors for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Some callers have no room to allocate: a host
+ * application that has already reserved almost all device memory for its own
+ * pool, or a time-critical loop that must not pay for cudaMalloc/cudaFree.
+ * This entry point allocates nothing: its scratch (instance table, labels,
+ * flags, edge list, counters, about 1.2 MB) is a fixed array in the library
+ * that every GPU loading the library holds until the process exits.
+ * Inputs are DEVICE arrays: bead_x [n_beads][3] FP64 positions (x in [0,nx),
+ * y in [0,ny)), bead_fil and bead_pos [n_beads] int32 (filament id, index in
+ * the filament; beads of a filament consecutive).  Output is a DEVICE array
+ * out[5] = {S_x, n_clusters, percolates, n_bonds, error bits (0 = ok)},
+ * written asynchronously on `stream`.  n_beads above LBM_NOALLOC_MAX_BEADS
+ * fails with LBM_ECAPACITY before any device work.  The first call on a
+ * device looks up the array's device address once (cudaGetSymbolAddress).
+ * Calls share the array: counters are cleared on every call, and two calls
+ * whose work overlaps on the GPU (other streams, other threads) race. */
+lbm_status lbm_deposit_descriptors_noalloc(const double* bead_x, const int* bead_fil,
+                                           const int* bead_pos, int n_beads, int nx, int ny,
+                                           double rcon, double x_src, double x_snk, double* out,
+                                           void* stream);
+
 /* ---------------------------------------------------------------------------
  * Sweep proposer: a small multilayer perceptron trained on deposit
  * descriptors of batched runs (no paper counterpart; the paper sweeps its

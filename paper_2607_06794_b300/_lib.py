@@ -17,7 +17,8 @@ FP64, FP32, FP16_SHIFTED, BF16_SHIFTED = range(4)
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_substrate_pattern", "lbm_add_nanowires",
            "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
            "lbm_deposit_descriptors", "lbm_destroy", "lbm_status_string", "lbm_mlp_param_count",
-           "lbm_mlp_scratch_bytes", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam")
+           "lbm_mlp_scratch_bytes", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
+           "lbm_deposit_descriptors_noalloc")
 
 
 class lbm_config(C.Structure):
@@ -96,6 +97,9 @@ def load():
     L.lbm_mlp_adam.restype = C.c_int
     L.lbm_mlp_adam.argtypes = [C.c_int, vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
                                C.c_double, C.c_int, vp]
+    L.lbm_deposit_descriptors_noalloc.restype = C.c_int
+    L.lbm_deposit_descriptors_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
+                                                  C.c_double, C.c_double, vp, vp]
     L.lbm_status_string.restype = C.c_char_p
     L.lbm_status_string.argtypes = [C.c_int]
     _lib = L

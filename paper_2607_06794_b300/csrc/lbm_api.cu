@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <random>
 #include <vector>
 
@@ -1061,3 +1062,81 @@ const char* lbm_status_string(lbm_status s) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Descriptors without any allocation: the same contact-graph kernels, with
+// their scratch (instance table, labels, flags, edge list, counters) in one
+// file-scope device array instead of a caller-provided workspace.
+// ===========================================================================
+namespace {
+
+constexpr int NOALLOC_MAX_BEADS = LBM_NOALLOC_MAX_BEADS;
+constexpr int NOALLOC_MAX_EDGES = 8 * NOALLOC_MAX_BEADS + 64;
+constexpr size_t NA_INST = 0;                                   // InstDev copy
+constexpr size_t NA_LAB = 1024;                                 // 3 x max int labels/flags
+constexpr size_t NA_EDGES = NA_LAB + sizeof(int) * 3 * (size_t)NOALLOC_MAX_BEADS;
+constexpr size_t NA_COUNT = NA_EDGES + sizeof(int2) * (size_t)NOALLOC_MAX_EDGES;  // edge counter
+constexpr size_t NA_ERR = NA_COUNT + 256;                                         // error bits
+constexpr size_t NA_BYTES = NA_ERR + 256;
+static_assert(sizeof(InstDev) <= NA_LAB, "instance table must fit its slot");
+
+// Held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Device address of the array per device, found once with that device current.
+unsigned char* g_noalloc_ptr[256] = {nullptr};
+std::mutex g_noalloc_mu;
+
+__global__ void k_noalloc_finish(const int* __restrict__ err, double* __restrict__ out) { out[4] = (double)*err; }
+
+}  // namespace
+
+extern "C" lbm_status lbm_deposit_descriptors_noalloc(const double* bead_x, const int* bead_fil,
+                                                      const int* bead_pos, int n_beads, int nx, int ny,
+                                                      double rcon, double x_src, double x_snk, double* out,
+                                                      void* stream) {
+    if (!bead_x || !bead_fil || !bead_pos || !out || n_beads < 1 || nx < 1 || ny < 1 || !(rcon > 0.0))
+        return LBM_EINVAL;
+    if (n_beads > NOALLOC_MAX_BEADS) return LBM_ECAPACITY;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return LBM_EINVAL;
+    unsigned char* base;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = (unsigned char*)p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    InstDev J{};
+    J.nx = nx;
+    J.ny = ny;
+    J.nb = n_beads;
+    J.nb_max = NOALLOC_MAX_BEADS;
+    J.bx = const_cast<double*>(bead_x);
+    J.bfil = const_cast<int*>(bead_fil);
+    J.bpos = const_cast<int*>(bead_pos);
+    J.rcon = rcon;
+    J.x_src = x_src;
+    J.x_snk = x_snk;
+    J.lab = (int*)(base + NA_LAB);
+    J.edges = (int2*)(base + NA_EDGES);
+    J.nedges = (int*)(base + NA_COUNT);
+    J.max_edges = NOALLOC_MAX_EDGES;
+    J.err = (int*)(base + NA_ERR);
+    J.desc = out;
+    InstDev* slot = (InstDev*)(base + NA_INST);
+    // pageable source: the copy has read J before the call returns
+    CK(cudaMemcpyAsync(slot, &J, sizeof(J), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(J.nedges, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(J.err, 0, sizeof(int), st));
+    k_desc_edges<<<(n_beads + 127) / 128, 128, 0, st>>>(slot, 0);
+    k_desc_solve<<<1, 1024, 0, st>>>(slot, 0);
+    k_noalloc_finish<<<1, 1, 0, st>>>(J.err, out);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
