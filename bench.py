@@ -119,21 +119,28 @@ def make_sim(wl):
 
 
 def launches_per_step(wl):
-    beads = any(w is not None and w[0] > 0 for w in wl.wires)
-    return 1 + ((4 + wl.cfgs[0].substeps) if beads else 0)
+    """Kernels of ours per step: fluid, column heights (when the sink can be on),
+    and for beads: flags/cells, fields, neighbour list, first kick, one force
+    launch per sub-step."""
+    n = 1 + (1 if any(c.J0 > 0 and c.evap_start >= 0 for c in wl.cfgs) else 0)
+    if any(w is not None and w[0] > 0 for w in wl.wires):
+        n += 4 + wl.cfgs[0].substeps
+    return n
 
 
-def cpu_baseline(wl, budget_s=12.0):
-    """The FP64 oracle on the host cores on whole steps of the same workload."""
+def oracle_workload(wl, nz=None):
+    """The FP64 oracle's state for the same workload: droplet, substrate, wires
+    (seeded straight wires inside the droplet, the same count and length)."""
     import numpy as np
 
     import oracle
     from tests import inputs
     c = wl.cfgs[0]
-    p = oracle.Params(c.nx, c.ny, c.nz, tau_R=c.tau_R, tau_B=c.tau_B, beta=c.beta, sigma=c.sigma,
+    nz = c.nz if nz is None else nz
+    p = oracle.Params(c.nx, c.ny, nz, tau_R=c.tau_R, tau_B=c.tau_B, beta=c.beta, sigma=c.sigma,
                       J0=c.J0, K=c.K, evap_start=c.evap_start, top_bc=c.top_bc, eps_coh=c.eps_coh,
                       xi=c.xi, gamma=c.gamma)
-    fR, fB = oracle.init_droplet(p, c.shape, c.cx, c.cy, c.cz, c.a, c.b, c.c, c.width)
+    fR, fB = oracle.init_droplet(p, c.shape, c.cx, c.cy, c.cz, c.a, c.b, min(c.c, nz - 4), c.width)
     th = wl.thetas[0] if wl.thetas[0] is not None else np.full((c.ny, c.nx), c.theta_deg)
     cot = oracle.cot_map(th)
     beads = None
@@ -141,10 +148,18 @@ def cpu_baseline(wl, budget_s=12.0):
         nw, L = wl.wires[0]
         nb = int(round(L / c.d0))
         lo = [c.cx - 0.6 * c.a, c.cy - 0.6 * c.b, 2.0]
-        hi = [c.cx + 0.6 * c.a, c.cy + 0.6 * c.b, 0.6 * c.c]
+        hi = [c.cx + 0.6 * c.a, c.cy + 0.6 * c.b, min(0.6 * c.c, nz - 3.0)]
         cen, dirs = inputs.random_filaments(c.seed, nw, nb, c.d0, lo, hi)
         fil, pos, X = inputs.straight_filaments(cen, dirs, nb, c.d0)
         beads = oracle.Beads(fil, pos, X)
+    return p, fR, fB, cot, beads
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """The FP64 oracle on the host cores on whole steps of the same workload."""
+    import oracle
+    c = wl.cfgs[0]
+    p, fR, fB, cot, beads = oracle_workload(wl)
     acc = oracle.Acc()
     oracle.step(p, fR, fB, cot, acc, beads)  # first step: page-in, not timed
     n, t0 = 0, time.perf_counter()
@@ -163,8 +178,6 @@ def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle itself on the host cores, same workload and metric."""
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
     from paper_2607_06794_b300 import workloads
     wl = workloads.WORKLOADS[args.workload]()
@@ -174,22 +187,18 @@ def run_reference(args, rank, world):
     nz = c.nz
     if (args.steps + args.warmup) * per_step > 180.0:
         nz = max(8, int(c.nz * 180.0 / ((args.steps + args.warmup) * per_step)))
-    p = oracle.Params(c.nx, c.ny, nz, tau_R=c.tau_R, tau_B=c.tau_B, beta=c.beta, sigma=c.sigma,
-                      J0=c.J0, K=c.K, evap_start=c.evap_start, top_bc=c.top_bc, eps_coh=c.eps_coh,
-                      xi=c.xi, gamma=c.gamma)
-    fR, fB = oracle.init_droplet(p, c.shape, c.cx, c.cy, c.cz, c.a, c.b, min(c.c, nz - 4), c.width)
-    th = wl.thetas[0] if wl.thetas[0] is not None else np.full((c.ny, c.nx), c.theta_deg)
-    cot = oracle.cot_map(th)
+    p, fR, fB, cot, beads = oracle_workload(wl, nz)
     acc = oracle.Acc()
     for _ in range(args.warmup):
-        oracle.step(p, fR, fB, cot, acc)
+        oracle.step(p, fR, fB, cot, acc, beads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.step(p, fR, fB, cot, acc)
+        oracle.step(p, fR, fB, cot, acc, beads)
     dt = time.perf_counter() - t0
     mlups = c.nx * c.ny * nz * args.steps / dt / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"whole FP64 oracle steps of {c.nx}x{c.ny}x{nz} (the {wl.name} droplet, fluid part)"
+    sample = (f"whole FP64 oracle steps of {c.nx}x{c.ny}x{nz} (the {wl.name} droplet, "
+              f"{0 if beads is None else beads.n} beads)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -200,6 +209,22 @@ def run_reference(args, rank, world):
                          "sample": sample},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def reduce_max(v, pg, device):
+    """Maximum of a scalar over all ranks (identity without a process group)."""
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, ms_max, world):
+    """Weak scaling: every rank advances its own lattices; the job's throughput is
+    all ranks' node updates over the slowest rank's time."""
+    return world * nodes_per_rank * steps / (ms_max * 1e-3) / 1e6
 
 
 def main():
@@ -233,11 +258,7 @@ def main():
         pg = dist
 
     def barrier_max(v):
-        if pg is None:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, pg, "cuda")
 
     mk = workloads.WORKLOADS[args.workload]
     wl = mk(args.prec) if args.prec else mk()
@@ -261,7 +282,7 @@ def main():
     clocks = clk.stop()
     ms = barrier_max(ms)
     ms_step = ms / args.steps
-    value = world * wl.nodes * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(wl.nodes, args.steps, ms, world)
 
     # roofline of the fused fluid kernel: CUDA events around every launch
     ms_fluid, ms_prof_step = sim.profile_steps(args.steps)

@@ -9,6 +9,9 @@
 
 namespace lbm {
 
+// beads a neighbour-search cell can hold (cells are at least rlist wide)
+constexpr int CELL_CAP = 32;
+
 // minimum image of a separation of two wrapped coordinates (|d| <= L)
 __device__ __forceinline__ double min_image(double d, int L) {
     const double h = 0.5 * L;
@@ -72,40 +75,51 @@ __device__ __forceinline__ long long tile_of(const InstDev& I, long long node) {
     return ((long long)(z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
 }
 
-// Step start: remember positions, flag the coupling tiles around every bead.
+// cell of a (finite, wrapped) position; cells are at least rlist wide
+__device__ __forceinline__ int cell_of(const InstDev& I, float x, float y, float z) {
+    int cx_ = (int)(x * I.cgx / I.nx), cy_ = (int)(y * I.cgy / I.ny), cz_ = (int)((z + 0.5f) * I.cgz / I.nz);
+    cx_ = min(max(cx_, 0), I.cgx - 1);
+    cy_ = min(max(cy_, 0), I.cgy - 1);
+    cz_ = min(max(cz_, 0), I.cgz - 1);
+    return (cz_ * I.cgy + cy_) * I.cgx + cx_;
+}
+
+// Step start, one warp per bead: remember the position, keep an FP32 copy
+// for the neighbour search, file the bead in its cell, and flag the coupling
+// tiles its trilinear stencil can reach during the step (lane = one corner of
+// the 4x4x2 reach; duplicates are harmless).
 __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
     const InstDev I = insts[blockIdx.y];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= I.nb) return;
     double X[3];
-    for (int d = 0; d < 3; ++d) X[d] = I.bx0[3 * a + d] = I.bx[3 * a + d];
+    for (int d = 0; d < 3; ++d) X[d] = I.bx[3 * a + d];
     if (!(isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]))) {
-        atomicOr(I.err, ERR_BEAD);
+        if (lane == 0) atomicOr(I.err, ERR_BEAD);
         return;
     }
-    X[2] = X[2] < -1.0 ? -1.0 : (X[2] > I.nz ? (double)I.nz : X[2]);
-    const int fx = wrapi((int)floor(X[0] - I.nx * floor(X[0] / I.nx)), I.nx);
-    const int fy = wrapi((int)floor(X[1] - I.ny * floor(X[1] / I.ny)), I.ny);
-    const int fz = (int)floor(X[2]);
-    int t8z[4], nzt = 0;
-    for (int dz = -1; dz <= 2; ++dz) {
-        int z = fz + dz;
-        z = z < 0 ? 0 : (z >= I.nz ? I.nz - 1 : z);
-        const int t = z >> 3;
-        bool seen = false;
-        for (int k = 0; k < nzt; ++k) seen |= t8z[k] == t;
-        if (!seen) t8z[nzt++] = t;
-    }
-    for (int dy = -1; dy <= 2; ++dy)
-        for (int dx = -1; dx <= 2; ++dx) {
-            const int x = wrapi(fx + dx, I.nx), y = wrapi(fy + dy, I.ny);
-            for (int k = 0; k < nzt; ++k) {
-                const int t = (t8z[k] * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
-                // most tiles are already flagged by a neighbour: read before the atomic
-                if (!((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u)
-                    I.tlist[atomicAdd(I.tcount, 1)] = t;
-            }
+    if (lane == 0) {
+        for (int d = 0; d < 3; ++d) {
+            I.bx0[3 * a + d] = X[d];
+            I.bxf[3 * a + d] = (float)X[d];
         }
+        const int c = cell_of(I, (float)X[0], (float)X[1], (float)X[2]);
+        const int slot = atomicAdd(I.ccount + c, 1);
+        if (slot < CELL_CAP)
+            I.cbeads[(size_t)c * CELL_CAP + slot] = a;
+        else
+            atomicOr(I.err, ERR_CAP);
+    }
+    const double zc = X[2] < -1.0 ? -1.0 : (X[2] > I.nz ? (double)I.nz : X[2]);
+    const int fx = wrapi((int)floor(X[0]), I.nx), fy = wrapi((int)floor(X[1]), I.ny), fz = (int)floor(zc);
+    const int dx = (lane & 3) - 1, dy = ((lane >> 2) & 3) - 1, dz = (lane >> 4) ? 2 : -1;
+    const int x = wrapi(fx + dx, I.nx), y = wrapi(fy + dy, I.ny);
+    int z = fz + dz;
+    z = z < 0 ? 0 : (z >= I.nz ? I.nz - 1 : z);
+    const int t = ((z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
+    // most tiles are already flagged by a neighbour: read before the atomic
+    if (!((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u) I.tlist[atomicAdd(I.tcount, 1)] = t;
 }
 
 // u* = (j + (F_s + body)/2)/rho and grad C on the nodes of flagged tiles.
@@ -244,33 +258,51 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     g[2] = gz;
 }
 
-// Verlet neighbour list for the step: pairs closer than rlist that are not
-// bonded or bending partners (those are handled by index).  One warp per
-// bead; lanes stride over the other beads and the list stays in index order.
+// Verlet neighbour list of the step, one warp per bead: lanes take the entries
+// of the 27 surrounding cells (FP32 positions; the skin absorbs the rounding).
 __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
     const InstDev I = insts[blockIdx.y];
     const int lane = threadIdx.x & 31;
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= I.nb) return;
-    const double xa = I.bx[3 * a], ya = I.bx[3 * a + 1], za = I.bx[3 * a + 2];
+    const float xa = I.bxf[3 * a], ya = I.bxf[3 * a + 1], za = I.bxf[3 * a + 2];
+    if (!(isfinite(xa) && isfinite(ya) && isfinite(za))) return;
+    const int c0 = cell_of(I, xa, ya, za);
+    const int ix = c0 % I.cgx, iy = (c0 / I.cgx) % I.cgy, iz = c0 / (I.cgx * I.cgy);
     const int fa = I.bfil[a], pa = I.bpos[a];
     const float r2 = (float)(I.rlist * I.rlist);
+    const float Lx = (float)I.nx, Ly = (float)I.ny;
+    const int nxo = min(3, I.cgx), nyo = min(3, I.cgy);  // distinct periodic neighbour cells
     int cnt = 0;
-    for (int b0 = 0; b0 < I.nb; b0 += 32) {
-        const int b = b0 + lane;
-        bool hit = false;
-        if (b < I.nb && b != a && !(I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2)) {
-            const float dx = (float)min_image(I.bx[3 * b] - xa, I.nx);
-            const float dy = (float)min_image(I.bx[3 * b + 1] - ya, I.ny);
-            const float dz = (float)(I.bx[3 * b + 2] - za);
-            hit = dx * dx + dy * dy + dz * dz < r2;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int zz = iz + dz;
+        if (zz < 0 || zz >= I.cgz) continue;
+        for (int oy = 0; oy < nyo; ++oy) {
+            const int yy = wrapi(iy + (nyo == 3 ? oy - 1 : oy), I.cgy);
+            for (int ox = 0; ox < nxo; ++ox) {
+                const int xx = wrapi(ix + (nxo == 3 ? ox - 1 : ox), I.cgx);
+                const int c = (zz * I.cgy + yy) * I.cgx + xx;
+                const int m = min(I.ccount[c], CELL_CAP);
+                bool hit = false;
+                int b = -1;
+                if (lane < m) {
+                    b = I.cbeads[(size_t)c * CELL_CAP + lane];
+                    if (b != a && !(I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2)) {
+                        float ex = I.bxf[3 * b] - xa, ey = I.bxf[3 * b + 1] - ya;
+                        const float ez = I.bxf[3 * b + 2] - za;
+                        ex = ex > 0.5f * Lx ? ex - Lx : (ex < -0.5f * Lx ? ex + Lx : ex);
+                        ey = ey > 0.5f * Ly ? ey - Ly : (ey < -0.5f * Ly ? ey + Ly : ey);
+                        hit = ex * ex + ey * ey + ez * ez < r2;
+                    }
+                }
+                const unsigned msk = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    const int k = cnt + __popc(msk & ((1u << lane) - 1u));
+                    if (k < I.max_nbr) I.nbr[(long long)a * I.max_nbr + k] = b;
+                }
+                cnt += __popc(msk);
+            }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-            const int k = cnt + __popc(m & ((1u << lane) - 1u));
-            if (k < I.max_nbr) I.nbr[(long long)a * I.max_nbr + k] = b;
-        }
-        cnt += __popc(m);
     }
     if (lane == 0) {
         if (cnt > I.max_nbr) {
@@ -281,7 +313,7 @@ __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
     }
 }
 
-// First half kick and drift of the step
+// First half kick and drift of the step (FP64 integration)
 __global__ void k_bead_kickdrift(const InstDev* __restrict__ insts) {
     const InstDev I = insts[blockIdx.y];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,13 +331,23 @@ __global__ void k_bead_kickdrift(const InstDev* __restrict__ insts) {
     for (int d = 0; d < 3; ++d) I.bx2[3 * a + d] = X[d];
 }
 
-// Force evaluation of sub-step s (1-based) at the current positions with the
-// half-step velocities, second half kick, reaction onto the fluid, and (not
-// last) the next first half kick and drift.
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Force evaluation of sub-step s (1-based), one warp per bead: lanes share the
+// bonded partners and the neighbour list (pair forces in the compute type),
+// lanes 0..7 take one stencil node each for the interpolation of u* and
+// grad C and for the reaction spread; lane 0 adds drag, solvation, adhesion
+// and friction and integrates in FP64 (second half kick; if not last, the next
+// first half kick and drift).
 template <typename T>
 __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     const InstDev I = insts[blockIdx.y];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= I.nb) return;
     const bool last = s == I.substeps;
     const double* cur = (s & 1) ? I.bx2 : I.bx;
@@ -313,97 +355,114 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
     int err = 0;
     const double P[3] = {cur[3 * a], cur[3 * a + 1], cur[3 * a + 2]};
-    const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     const int fa = I.bfil[a], pa = I.bpos[a];
-    // pair forces in the compute type (FP32 outside the FP64 validation path),
-    // summed in FP64 like the integration
-    double f[3] = {0.0, 0.0, 0.0};
-    auto pair = [&](int b, bool same, int sep) {
-        const T d[3] = {(T)min_image(cur[3 * b] - P[0], I.nx), (T)min_image(cur[3 * b + 1] - P[1], I.ny),
-                        (T)(cur[3 * b + 2] - P[2])};
-        const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const int nn = I.nnbr[a];
+    // ---- pair forces, candidates spread over the lanes ----
+    T fx = 0, fy = 0, fz = 0;
+    for (int c = lane; c < 4 + nn; c += 32) {
+        int b;
+        bool same;
+        int sep;
+        if (c < 4) {
+            const int k = c < 2 ? c - 2 : c - 1;  // -2, -1, +1, +2
+            b = a + k;
+            if (b < 0 || b >= I.nb || I.bfil[b] != fa || I.bpos[b] - pa != k) continue;
+            same = true;
+            sep = k < 0 ? -k : k;
+        } else {
+            b = I.nbr[(long long)a * I.max_nbr + (c - 4)];
+            same = I.bfil[b] == fa;
+            sep = same ? abs(I.bpos[b] - pa) : 0;
+        }
+        const T d0 = (T)min_image(cur[3 * b] - P[0], I.nx), d1 = (T)min_image(cur[3 * b + 1] - P[1], I.ny),
+                d2 = (T)(cur[3 * b + 2] - P[2]);
+        const T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         const T g = pair_dUdr<T>(I, same, sep, r, err);
         if (g != T(0)) {
             const T gr = g / r;
-            for (int k = 0; k < 3; ++k) f[k] += (double)(gr * d[k]);
+            fx += gr * d0;
+            fy += gr * d1;
+            fz += gr * d2;
         }
-    };
-    for (int k = -2; k <= 2; ++k) {
-        const int b = a + k;
-        if (k == 0 || b < 0 || b >= I.nb) continue;
-        if (I.bfil[b] == fa && I.bpos[b] - pa == k) pair(b, true, k < 0 ? -k : k);
     }
-    const int nn = I.nnbr[a];
-    for (int k = 0; k < nn; ++k) {
-        const int b = I.nbr[(long long)a * I.max_nbr + k];
-        const bool same = I.bfil[b] == fa;
-        pair(b, same, same ? abs(I.bpos[b] - pa) : 0);
-    }
-    // fluid coupling: drag towards the local velocity and solvation along grad C
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    // ---- interpolation of u* and grad C, one stencil node per lane ----
     long long id[8];
     double w[8];
     stencil(I, P, id, w);
-    double u[3] = {0, 0, 0}, g[3] = {0, 0, 0};
-    const T* ust = (const T*)I.ust;
-    const T* gcl = (const T*)I.gcol;
-    for (int k = 0; k < 8; ++k)
+    T u[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
+    if (lane < 8) {
+        const T* ust = (const T*)I.ust + 3 * id[lane];
+        const T* gcl = (const T*)I.gcol + 3 * id[lane];
+        const T wl = (T)w[lane];
         for (int d = 0; d < 3; ++d) {
-            u[d] += w[k] * (double)ust[3 * id[k] + d];
-            g[d] += w[k] * (double)gcl[3 * id[k] + d];
+            u[d] = wl * ust[d];
+            gc[d] = wl * gcl[d];
         }
-    double drag[3];
-    for (int d = 0; d < 3; ++d) {
-        drag[d] = I.gamma * (u[d] - vh[d]);
-        f[d] += drag[d] + I.xi * g[d];
     }
-    // substrate adhesion (LJ at the image distance) and load-dependent friction
-    const double rw = 2.0 * (P[2] + 0.5);
-    double fw = 0.0;
-    if (I.eps_s > 0.0 && rw < I.rc && rw > 0.0) fw = -2.0 * I.eps_s * lj_shape_dr<double>(I.d0, rw);
-    if (I.eps_s > 0.0 && rw < I.rc) {
-        const double load = (f[2] < 0.0 ? -f[2] : 0.0) + (fw < 0.0 ? -fw : 0.0);
-        const double vt = sqrt(vh[0] * vh[0] + vh[1] * vh[1]);
-        if (vt > 0.0) {
-            double mag = I.gamma_t * vt;
-            if (mag > I.mu * load) mag = I.mu * load;
-            f[0] -= mag * vh[0] / vt;
-            f[1] -= mag * vh[1] / vt;
+    for (int d = 0; d < 3; ++d) {
+        u[d] = warp_sum(u[d]);
+        gc[d] = warp_sum(gc[d]);
+    }
+    const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
+    T drag[3];
+    for (int d = 0; d < 3; ++d) drag[d] = (T)I.gamma * (u[d] - (T)vh[d]);
+    T f[3] = {fx + drag[0] + (T)I.xi * gc[0], fy + drag[1] + (T)I.xi * gc[1], fz + drag[2] + (T)I.xi * gc[2]};
+    // ---- substrate adhesion (LJ at the image distance) and load-dependent friction ----
+    const T rw = T(2) * ((T)P[2] + T(0.5));
+    T fw = 0;
+    if (I.eps_s > 0.0 && rw < (T)I.rc && rw > T(0)) fw = T(-2) * (T)I.eps_s * lj_shape_dr<T>((T)I.d0, rw);
+    if (I.eps_s > 0.0 && rw < (T)I.rc) {
+        const T load = (f[2] < T(0) ? -f[2] : T(0)) + (fw < T(0) ? -fw : T(0));
+        const T vx = (T)vh[0], vy = (T)vh[1];
+        const T vt = sqrt(vx * vx + vy * vy);
+        if (vt > T(0)) {
+            T mag = (T)I.gamma_t * vt;
+            if (mag > (T)I.mu * load) mag = (T)I.mu * load;
+            f[0] -= mag * vx / vt;
+            f[1] -= mag * vy / vt;
         }
     }
     f[2] += fw;
-    // reaction of the drag onto the fluid, only inside flagged tiles
-    T* fe = (T*)I.fext;
-    for (int k = 0; k < 8; ++k) {
-        if (!I.tflag[tile_of(I, id[k])]) {
+    // ---- reaction of the drag onto the fluid, one stencil node per lane ----
+    if (lane < 8) {
+        if (I.tflag[tile_of(I, id[lane])]) {
+            T* fe = (T*)I.fext + 3 * id[lane];
+            const T c = (T)(-dt * w[lane]);
+            for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
+        } else {
             err |= ERR_BEAD;
-            continue;
         }
-        for (int d = 0; d < 3; ++d) atomicAdd(fe + 3 * id[k] + d, (T)(-dt * w[k] * drag[d]));
     }
-    double v[3];
-    for (int d = 0; d < 3; ++d) {
-        I.bF[3 * a + d] = f[d];
-        v[d] = vh[d] + hk * f[d];
-    }
-    if (!last) {
-        double X[3];
+    // ---- FP64 integration on lane 0 ----
+    if (lane == 0) {
+        double v[3];
         for (int d = 0; d < 3; ++d) {
-            const double v2 = v[d] + hk * f[d];
-            I.bvh[3 * a + d] = v2;
-            X[d] = P[d] + dt * v2;
+            I.bF[3 * a + d] = (double)f[d];
+            v[d] = vh[d] + hk * (double)f[d];
         }
-        X[0] -= I.nx * floor(X[0] / I.nx);
-        X[1] -= I.ny * floor(X[1] / I.ny);
-        if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) err |= ERR_BEAD;
-        for (int d = 0; d < 3; ++d) nxt[3 * a + d] = X[d];
-    } else {
-        for (int d = 0; d < 3; ++d) {
-            I.bv[3 * a + d] = v[d];
-            if (cur != I.bx) I.bx[3 * a + d] = P[d];
+        if (!last) {
+            double X[3];
+            for (int d = 0; d < 3; ++d) {
+                const double v2 = v[d] + hk * (double)f[d];
+                I.bvh[3 * a + d] = v2;
+                X[d] = P[d] + dt * v2;
+            }
+            X[0] -= I.nx * floor(X[0] / I.nx);
+            X[1] -= I.ny * floor(X[1] / I.ny);
+            if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) err |= ERR_BEAD;
+            for (int d = 0; d < 3; ++d) nxt[3 * a + d] = X[d];
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                I.bv[3 * a + d] = v[d];
+                if (cur != I.bx) I.bx[3 * a + d] = P[d];
+            }
+            const double dx = min_image(P[0] - I.bx0[3 * a], I.nx),
+                         dy = min_image(P[1] - I.bx0[3 * a + 1], I.ny), dz = P[2] - I.bx0[3 * a + 2];
+            if (dx * dx + dy * dy + dz * dz > 0.25) err |= ERR_BEAD;
         }
-        const double dx = min_image(P[0] - I.bx0[3 * a], I.nx),
-                     dy = min_image(P[1] - I.bx0[3 * a + 1], I.ny), dz = P[2] - I.bx0[3 * a + 2];
-        if (dx * dx + dy * dy + dz * dz > 0.25) err |= ERR_BEAD;
     }
     if (err) atomicOr(I.err, err);
 }

@@ -56,6 +56,15 @@ struct Layout {
     int ntiles = 0;
 };
 
+// neighbour-list radius: the longest interaction range plus a skin of one
+// lattice unit (beads move less than half a unit per step)
+double rlist_of(const lbm_config& c) {
+    double rl = c.d0;
+    if (c.eps_coh > 0) rl = std::max(rl, c.rc);
+    rl = std::max(rl, c.rcon);
+    return rl + 1.0;
+}
+
 int chunk_z(const lbm_config& c, const Shape& sh) {
     if (sh.chunk > 0) return std::max(2, std::min(sh.chunk, c.nz));
     // enough blocks to fill the GPU on small lattices
@@ -133,6 +142,14 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.nbr = (int*)cv.take(sizeof(int) * (size_t)c.max_beads * MAX_NBR);
             I.nnbr = (int*)cv.take(sizeof(int) * c.max_beads);
             I.lab = (int*)cv.take(sizeof(int) * 3 * (size_t)c.max_beads);
+            const double rl = rlist_of(c);
+            I.cgx = std::max(1, (int)floor(c.nx / rl));
+            I.cgy = std::max(1, (int)floor(c.ny / rl));
+            I.cgz = std::max(1, (int)floor(c.nz / rl));
+            const size_t ncell = (size_t)I.cgx * I.cgy * I.cgz;
+            I.ccount = (int*)cv.take(sizeof(int) * ncell);
+            I.cbeads = (int*)cv.take(sizeof(int) * ncell * CELL_CAP);
+            I.bxf = (float*)cv.take(sizeof(float) * 3 * (size_t)c.max_beads);
             I.max_edges = 8 * c.max_beads + 64;
             I.edges = (int2*)cv.take(sizeof(int2) * (size_t)I.max_edges);
             I.nedges = (int*)cv.take(sizeof(int));
@@ -232,23 +249,23 @@ lbm_status launch_beads(lbm_handle* h) {
     using T = typename S::T;
     const int n = (int)h->cfg.size();
     if (h->max_nb == 0) return LBM_OK;
-    // clear all coupling-tile flags (contiguous per instance; one memset each)
+    // clear the coupling-tile flags and the cell counts of every instance with beads
     for (int k = 0; k < n; ++k) {
         const InstDev& I = h->L.inst[k];
-        if (I.tflag)
-            CK(cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int),
-                               h->stream));
+        if (!I.tflag) continue;
+        CK(cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int), h->stream));
+        CK(cudaMemsetAsync(I.ccount, 0, sizeof(int) * (size_t)I.cgx * I.cgy * I.cgz, h->stream));
     }
-    const int bt = 64;  // small blocks spread the few hundred beads over many SMs
-    const dim3 gb((h->max_nb + bt - 1) / bt, n);
-    k_bead_begin<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
+    const dim3 gw((h->max_nb * 32 + 255) / 256, n);  // one warp per bead
+    const dim3 gt((h->max_nb + 63) / 64, n);         // one thread per bead
+    k_bead_begin<<<gw, 256, 0, h->stream>>>(h->L.d_inst);
     int maxt = 0;
     for (auto& I : h->L.inst) maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
     k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
-    k_bead_nlist<<<dim3((h->max_nb * 32 + 255) / 256, n), 256, 0, h->stream>>>(h->L.d_inst);
-    k_bead_kickdrift<<<gb, bt, 0, h->stream>>>(h->L.d_inst);
+    k_bead_nlist<<<gw, 256, 0, h->stream>>>(h->L.d_inst);
+    k_bead_kickdrift<<<gt, 64, 0, h->stream>>>(h->L.d_inst);
     const int S_ = h->cfg[0].substeps;
-    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<gb, bt, 0, h->stream>>>(h->L.d_inst, s);
+    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<gw, 256, 0, h->stream>>>(h->L.d_inst, s);
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -655,10 +672,7 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
         I.mu = c.mu;
         I.gamma_t = c.gamma_t;
         I.mass = c.bead_mass;
-        double rl = c.d0;
-        if (c.eps_coh > 0) rl = std::max(rl, c.rc);
-        rl = std::max(rl, c.rcon);
-        I.rlist = rl + 1.0;
+        I.rlist = rlist_of(c);
         I.rcon = c.rcon;
         I.x_src = c.x_src;
         I.x_snk = c.x_snk;

@@ -208,6 +208,11 @@ struct InstDev {
     int* nbr;
     int* nnbr;
     double ks, Rm, d0, eps_wca, kb, eps_coh, eps_s, rc, gamma, xi, mu, gamma_t, mass, rlist;
+    // cell list of large instances (cells at least rlist wide)
+    int cgx, cgy, cgz, pad2;
+    int* ccount;                 // beads filed per cell this step
+    int* cbeads;                 // [cell][CELL_CAP] bead ids
+    float* bxf;                  // [n][3] FP32 copy of the step-start positions
     // descriptors
     double rcon, x_src, x_snk;
     int* lab;
@@ -237,7 +242,7 @@ struct Vec4<float> {
 };
 template <>
 struct Vec4<double> {
-    using type = double4;
+    using type = double4_16a;
 };
 
 __host__ __device__ inline int wrapi(int a, int n) {

@@ -306,3 +306,27 @@ def test_full_size_c2_step_in_bench_configuration(lbm, oracle):
     assert np.allclose(sim.read(0, "bead_x"), ob.X, atol=1e-6)
     a = sim.read(0, "accum")
     assert a[2] == pytest.approx(acc.evaporated, rel=1e-4)
+
+
+def test_large_bead_instance_uses_cell_list_and_matches_oracle(lbm, oracle):
+    """More beads than one block holds: cell-list neighbour search and one launch per sub-step."""
+    cfg = droplet_cfg(lbm, nx=96, ny=64, nz=24, prec="fp64", max_beads=1400, eps_coh=0.006, xi=0.02,
+                      a=40, b=26, c=16)
+    p, fR, fB, cot = oracle_state(oracle, cfg, 2)
+    lo = [cfg.cx - 34, cfg.cy - 20, 2.5]
+    hi = [cfg.cx + 34, cfg.cy + 20, 13.0]
+    cen, dirs = inputs.random_filaments(31, 270, 4, cfg.d0, lo, hi, min_dist=2.05)
+    assert len(cen) == 270  # 1080 beads: more than one block holds
+    fil, pos, X = inputs.straight_filaments(cen, dirs, 4, cfg.d0)
+    sim = lbm.Simulation([cfg])
+    sim.write(0, "populations", np.stack([fR, fB]))
+    sim.add_nanowires(0, 270, 8.0, cen, dirs)
+    ob = oracle.Beads(fil, pos, sim_free_positions(cen, dirs, 4, cfg))
+    acc = oracle.Acc()
+    for _ in range(2):
+        oracle.step(p, fR, fB, cot, acc, ob)
+    sim.step(2)
+    sim.sync()
+    assert np.allclose(sim.read(0, "bead_x"), ob.X, atol=1e-11)
+    assert np.allclose(sim.read(0, "bead_f"), ob.F, atol=1e-11)
+    assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-11
