@@ -6,6 +6,8 @@
 // wetting paragraphs).
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -68,6 +70,16 @@ __device__ __forceinline__ int wrap_near(int a, int n) {
     while (a < 0) a += n;
     while (a >= n) a -= n;
     return a;
+}
+
+// compile-time loop over lattice directions: f(std::integral_constant<int, I>)
+// for I in [B, E); every c_i and w_i folds to a constant in the body
+template <int B, int E, int STEP = 1, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + STEP, E, STEP>(f);
+    }
 }
 
 template <typename T>
@@ -249,15 +261,15 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 const int sy = s / HX1, sx = s - sy * HX1;
                 if (sx > tw + 1 || sy > th + 1) continue;
                 T gx = 0, gy = 0, gz = 0;
-#pragma unroll
-                for (int i = 1; i < 19; ++i) {
+                static_for<1, 19>([&](auto I_) {
+                    constexpr int i = decltype(I_)::value;
                     const int rr = cz(i) < 0 ? rm : (cz(i) > 0 ? rp : r0);
                     const T c = sC[rr][sy + 1 + cy(i)][sx + 1 + cx(i)];
-                    const T w = (T)wq(i);
-                    if (cx(i)) gx += w * cx(i) * c;
-                    if (cy(i)) gy += w * cy(i) * c;
-                    if (cz(i)) gz += w * cz(i) * c;
-                }
+                    constexpr T w = (T)wq(i);
+                    if constexpr (cx(i) != 0) gx += w * cx(i) * c;
+                    if constexpr (cy(i) != 0) gy += w * cy(i) * c;
+                    if constexpr (cz(i) != 0) gz += w * cz(i) * c;
+                });
                 gx *= T(3);
                 gy *= T(3);
                 gz *= T(3);
@@ -357,8 +369,8 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         // ---- phase 1: raw pull loads of plane z, flush, C ring upkeep ----
         E rawR[19], rawB[19];
         if (active) {
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
+            static_for<0, 19>([&](auto I_) {
+                constexpr int i = decltype(I_)::value;
                 const int sz = z - cz(i);
                 unsigned k;
                 if (sz < 0 || (sz >= nz && top_bc == 0)) {
@@ -372,7 +384,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 }
                 rawR[i] = __ldg(src + k);
                 rawB[i] = __ldg(src + cs + k);
-            }
+            });
         }
         flush(z - 2);
         commitC();
@@ -386,8 +398,8 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             T Fi[19];
             T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
             const bool top_gas = z == nz - 1 && top_bc == 1;
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
+            static_for<0, 19>([&](auto I_) {
+                constexpr int i = decltype(I_)::value;
                 T r, b;
                 const bool bb = (z - cz(i) < 0) || (z - cz(i) >= nz && top_bc == 0);
                 if (top_gas && cz(i) < 0) {
@@ -405,29 +417,30 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 rR += r;
                 rB += b;
                 Fi[i] = r + b;
-                if (cx(i)) jx += cx(i) * Fi[i];
-                if (cy(i)) jy += cy(i) * Fi[i];
-                if (cz(i)) jz += cz(i) * Fi[i];
-            }
+                if constexpr (cx(i) != 0) jx += cx(i) * Fi[i];
+                if constexpr (cy(i) != 0) jy += cy(i) * Fi[i];
+                if constexpr (cz(i) != 0) jz += cz(i) * Fi[i];
+            });
             if (top_gas) {
-#pragma unroll
-                for (int i = 0; i < 19; ++i)
-                    if (cz(i) > 0) {
+                static_for<0, 19>([&](auto I_) {
+                    constexpr int i = decltype(I_)::value;
+                    if constexpr (cz(i) > 0) {
                         T r, b;
                         S::load(src, cs, (unsigned)i * N + node, (T)wq(i), rho0, r, b);
                         top_out += r + b;
                     }
+                });
             }
             T kap = 0;
-#pragma unroll
-            for (int i = 1; i < 19; ++i) {
+            static_for<1, 19>([&](auto I_) {
+                constexpr int i = decltype(I_)::value;
                 const V4 nn = sN[rz[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
                 T d = 0;
-                if (cx(i)) d += cx(i) * nn.x;
-                if (cy(i)) d += cy(i) * nn.y;
-                if (cz(i)) d += cz(i) * nn.z;
+                if constexpr (cx(i) != 0) d += cx(i) * nn.x;
+                if constexpr (cy(i) != 0) d += cy(i) * nn.y;
+                if constexpr (cz(i) != 0) d += cz(i) * nn.z;
                 kap += (T)wq(i) * d;
-            }
+            });
             kap *= T(-3);
             const V4 G = sG[z & 1][ty][tx];
             const T Gx = G.x, Gy = G.y, Gz = G.z;
@@ -460,12 +473,13 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             }
             const T rGx = Gx * ig, rGy = Gy * ig, rGz = Gz * ig;
             const T base0 = T(1) - T(1.5) * usq;
-            auto emit = [&](int i, T post) {
-                const T w = (T)wq(i);
+            auto emit = [&](auto I_, T post) {
+                constexpr int i = decltype(I_)::value;
+                constexpr T w = (T)wq(i);
                 T cG = 0;
-                if (cx(i)) cG += cx(i) * rGx;
-                if (cy(i)) cG += cy(i) * rGy;
-                if (cz(i)) cG += cz(i) * rGz;
+                if constexpr (cx(i) != 0) cG += cx(i) * rGx;
+                if constexpr (cy(i) != 0) cG += cy(i) * rGy;
+                if constexpr (cz(i) != 0) cG += cz(i) * rGz;
                 T r = phi * post + coef * w * (cG * (T)inv_len(i));
                 T b = post - r;
                 if (i == 0 && evap_on) {
@@ -491,33 +505,35 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 }
             };
             {  // rest direction
-                const T w = (T)wq(0);
+                constexpr T w = (T)wq(0);
                 const T feq = w * rho * base0;
                 const T Sg = gsrc * w * (T(-3) * uF);
-                emit(0, Fi[0] - omega * (Fi[0] - feq) + Sg);
+                emit(std::integral_constant<int, 0>{}, Fi[0] - omega * (Fi[0] - feq) + Sg);
             }
-#pragma unroll
-            for (int i = 1; i < 19; i += 2) {
+            static_for<1, 19, 2>([&](auto I_) {
                 // the pair (i, opp(i) = i+1) shares c.u, c.F and c.G up to sign
-                const T w = (T)wq(i);
+                constexpr int i = decltype(I_)::value;
+                constexpr T w = (T)wq(i);
                 T cu = 0, cF = 0;
-                if (cx(i)) { cu += cx(i) * ux; cF += cx(i) * Fx; }
-                if (cy(i)) { cu += cy(i) * uy; cF += cy(i) * Fy; }
-                if (cz(i)) { cu += cz(i) * uz; cF += cz(i) * Fz; }
+                if constexpr (cx(i) != 0) { cu += cx(i) * ux; cF += cx(i) * Fx; }
+                if constexpr (cy(i) != 0) { cu += cy(i) * uy; cF += cy(i) * Fy; }
+                if constexpr (cz(i) != 0) { cu += cz(i) * uz; cF += cz(i) * Fz; }
                 const T wr = w * rho;
                 const T even = wr * (base0 + T(4.5) * cu * cu);
                 const T odd = wr * (T(3) * cu);
                 const T se = gsrc * w * (T(9) * cu * cF - T(3) * uF);
                 const T so = gsrc * w * (T(3) * cF);
-                emit(i, Fi[i] - omega * (Fi[i] - (even + odd)) + (se + so));
-                emit(i + 1, Fi[i + 1] - omega * (Fi[i + 1] - (even - odd)) + (se - so));
-            }
+                emit(std::integral_constant<int, i>{}, Fi[i] - omega * (Fi[i] - (even + odd)) + (se + so));
+                emit(std::integral_constant<int, i + 1>{},
+                     Fi[i + 1] - omega * (Fi[i + 1] - (even - odd)) + (se - so));
+            });
             if (top_gas) {
                 // gas inflow that the next stream brings to this node
                 T inB = 0;
-#pragma unroll
-                for (int i = 0; i < 19; ++i)
-                    if (cz(i) < 0) inB += (T)wq(i) * rho0;
+                static_for<0, 19>([&](auto I_) {
+                    constexpr int i = decltype(I_)::value;
+                    if constexpr (cz(i) < 0) inB += (T)wq(i) * rho0;
+                });
                 atomicAdd(&sA[rz[1]][ty + 1][tx + 1][1], inB);
             }
         }
