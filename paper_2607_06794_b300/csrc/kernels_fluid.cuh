@@ -6,6 +6,7 @@
 // wetting paragraphs).
 #pragma once
 
+#include <cstring>
 #include <type_traits>
 
 #include "lbm_internal.cuh"
@@ -82,6 +83,26 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
+// 4-byte asynchronous global->shared copies (completion tracked per thread)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N_>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory");
+}
+
+// raw 16-bit element k of a buffer, from the 4-byte word that holds it
+template <class E>
+__device__ __forceinline__ E half_of(unsigned word, unsigned k) {
+    const unsigned short bits = (unsigned short)((k & 1u) ? (word >> 16) : (word & 0xffffu));
+    E e;
+    memcpy(&e, &bits, 2);
+    return e;
+}
+
 template <typename T>
 __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
 template <>
@@ -138,9 +159,13 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     using V4 = typename Vec4<T>::type;
     __shared__ V4 sN[3][HY1][HX1];
     __shared__ V4 sG[2][TY][TX];
-    __shared__ T sA[3][HY1][HX1][2];
+    __shared__ T sA[3][2][HY1][HX1];  // component outer: conflict-free pushes
     __shared__ double sRed[NT / 32][3];
     __shared__ int sErr;
+    // pulled populations of the next plane, staged by asynchronous 4-byte copies
+    // (16- and 32-bit storage; FP64 keeps them in registers): [38][NT] words
+    constexpr bool ASYNC = sizeof(E) == 4;
+    extern __shared__ __align__(16) unsigned stage_dyn[];
 
     const TileDesc td = tiles[blockIdx.x];
     const InstDev& Ig = insts[td.inst];
@@ -205,7 +230,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
 
     const T hcol = (evap_on && active) ? hcolm[y * nx + x] : T(0);
 
-    for (int s = tid; s < 3 * HY1 * HX1 * 2; s += NT) (&sA[0][0][0][0])[s] = T(0);
+    for (int s = tid; s < 3 * 2 * HY1 * HX1; s += NT) (&sA[0][0][0][0])[s] = T(0);
     if (tid == 0) sErr = 0;
 
     // C of plane p into the ring over the tile plus 2 cells (synchronous form)
@@ -312,9 +337,9 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         for (int s = tid; s < HX1 * HY1; s += NT) {
             const int sy = s / HX1, sx = s - sy * HX1;
             if (sx > tw + 1 || sy > th + 1) continue;
-            const T a0 = sA[r][sy][sx][0], a1 = sA[r][sy][sx][1];
-            sA[r][sy][sx][0] = T(0);
-            sA[r][sy][sx][1] = T(0);
+            const T a0 = sA[r][0][sy][sx], a1 = sA[r][1][sy][sx];
+            sA[r][0][sy][sx] = T(0);
+            sA[r][1][sy][sx] = T(0);
             if (q < 0 || q >= nz) continue;
             const int gx = wrap_near(x0 - 1 + sx, nx), gy = wrap_near(y0 - 1 + sy, ny);
             const unsigned n = (unsigned)q * nxy + (unsigned)gy * nx + gx;
@@ -340,6 +365,36 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const unsigned rowm = (unsigned)ym * nx, row0 = (unsigned)y * nx, rowp = (unsigned)yp * nx;
 
+    // element of direction i that streams into this thread's node of plane z
+    auto pull_index = [&](int z, int i) -> unsigned {
+        const unsigned node = (unsigned)z * nxy + row0 + x;
+        const int sz = z - cz(i);
+        if (sz < 0 || (sz >= nz && top_bc == 0)) return (unsigned)opp(i) * N + node;  // bounce-back
+        if (sz >= nz) return (unsigned)i * N + node;  // replaced by the gas inflow
+        const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
+        const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
+        return (unsigned)i * N + (unsigned)sz * nxy + row + sx;
+    };
+    // asynchronous pull of plane z into the stage (one commit group per plane);
+    // every slot is read and written by its own thread only
+    auto issue_pull = [&](int z) {
+        if (active && z < z1) {
+            unsigned* st = stage_dyn + tid;
+            static_for<0, 19>([&](auto I_) {
+                constexpr int i = decltype(I_)::value;
+                const unsigned k = pull_index(z, i);
+                if constexpr (sizeof(E) == 4) {
+                    cp_async4(st + (size_t)i * NT, src + k);
+                    cp_async4(st + (size_t)(19 + i) * NT, src + cs + k);
+                } else {
+                    cp_async4(st + (size_t)i * NT, (const unsigned*)src + (k >> 1));
+                    cp_async4(st + (size_t)(19 + i) * NT, (const unsigned*)src + ((cs + k) >> 1));
+                }
+            });
+        }
+        cp_async_commit();
+    };
+
     // ---- prologue: C planes and normals below the first plane ----
     if (z0 == 0) {
         loadC(-1);
@@ -361,27 +416,20 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         computeN(z0);
     }
     prefetchC(z0 + 2);
+    if constexpr (ASYNC) issue_pull(z0);
     __syncthreads();
 
     for (int z = z0; z < z1; ++z) {
         const unsigned node = (unsigned)z * nxy + row0 + x;
         const int rz[3] = {ring(z - 1), ring(z), ring(z + 1)};  // ring slots of planes z-1, z, z+1
         // ---- phase 1: raw pull loads of plane z, flush, C ring upkeep ----
-        E rawR[19], rawB[19];
-        if (active) {
+        E rawR[ASYNC ? 1 : 19], rawB[ASYNC ? 1 : 19];
+        if constexpr (ASYNC) {
+            // plane z was issued at the end of the previous plane (or before the loop)
+        } else if (active) {
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                const int sz = z - cz(i);
-                unsigned k;
-                if (sz < 0 || (sz >= nz && top_bc == 0)) {
-                    k = (unsigned)opp(i) * N + node;  // half-way bounce-back
-                } else if (sz >= nz) {
-                    k = (unsigned)i * N + node;  // replaced by the gas inflow below
-                } else {
-                    const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
-                    const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
-                    k = (unsigned)i * N + (unsigned)sz * nxy + row + sx;
-                }
+                const unsigned k = pull_index(z, i);
                 rawR[i] = __ldg(src + k);
                 rawB[i] = __ldg(src + cs + k);
             });
@@ -398,21 +446,38 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             T Fi[19];
             T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
             const bool top_gas = z == nz - 1 && top_bc == 1;
+            if constexpr (ASYNC) cp_async_wait<0>();  // plane z landed
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
+                E eR, eB;
+                if constexpr (ASYNC) {
+                    const unsigned* st = stage_dyn + tid;
+                    const unsigned wR = st[(size_t)i * NT], wB = st[(size_t)(19 + i) * NT];
+                    if constexpr (sizeof(E) == 4) {
+                        eR = __uint_as_float(wR);
+                        eB = __uint_as_float(wB);
+                    } else {
+                        const unsigned k = pull_index(z, i);
+                        eR = half_of<E>(wR, k);
+                        eB = half_of<E>(wB, cs + k);
+                    }
+                } else {
+                    eR = rawR[i];
+                    eB = rawB[i];
+                }
                 T r, b;
                 const bool bb = (z - cz(i) < 0) || (z - cz(i) >= nz && top_bc == 0);
                 if (top_gas && cz(i) < 0) {
                     // pure-gas equilibrium streams in; what streamed out is booked
                     T ro, bo;
-                    S::decode(rawR[i], rawB[i], (T)wq(i), rho0, ro, bo);
+                    S::decode(eR, eB, (T)wq(i), rho0, ro, bo);
                     (void)ro;
                     (void)bo;
                     r = T(0);
                     b = (T)wq(i) * rho0;
                     top_in += b;
                 } else {
-                    S::decode(rawR[i], rawB[i], (T)wq(bb ? opp(i) : i), rho0, r, b);
+                    S::decode(eR, eB, (T)wq(bb ? opp(i) : i), rho0, r, b);
                 }
                 rR += r;
                 rB += b;
@@ -494,14 +559,14 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 const int tz = z + cz(i);
                 T* a;
                 if (tz < 0 || (tz >= nz && top_bc == 0))
-                    a = sA[rz[1]][ty + 1][tx + 1];  // bounces back to this node
+                    a = &sA[rz[1]][0][ty + 1][tx + 1];  // bounces back to this node
                 else if (tz < nz)
-                    a = sA[rz[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                    a = &sA[rz[cz(i) + 1]][0][ty + 1 + cy(i)][tx + 1 + cx(i)];
                 else
                     a = nullptr;
                 if (a) {
                     atomicAdd(a, rq);
-                    atomicAdd(a + 1, bq);
+                    atomicAdd(a + HY1 * HX1, bq);
                 }
             };
             {  // rest direction
@@ -534,11 +599,13 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     constexpr int i = decltype(I_)::value;
                     if constexpr (cz(i) < 0) inB += (T)wq(i) * rho0;
                 });
-                atomicAdd(&sA[rz[1]][ty + 1][tx + 1][1], inB);
+                atomicAdd(&sA[rz[1]][1][ty + 1][tx + 1], inB);
             }
         }
+        if constexpr (ASYNC) issue_pull(z + 1);  // its slots were consumed above by this thread
         __syncthreads();
     }
+    if constexpr (ASYNC) cp_async_wait<0>();
     // the remaining planes touch disjoint ring slots
     flush(z1 - 2);
     flush(z1 - 1);

@@ -24,7 +24,7 @@ struct Shape {
     int tx, ty, chunk;
 };
 const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {64, 4, 0}, {64, 4, 16},
-                        {32, 4, 0}, {32, 4, 16}, {64, 8, 0}, {64, 8, 32}};
+                        {32, 4, 0}, {32, 4, 16}, {32, 4, 32}, {64, 4, 32}};
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 64;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
@@ -111,7 +111,8 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
         I.top_bc = c.top_bc;
         I.N = (long long)c.nx * c.ny * c.nz;
         const size_t eb = elem_bytes(c.prec), cb = comp_bytes(c.prec);
-        for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb);
+        // +16 bytes: 16-bit storage is staged in 4-byte words that may reach 2 bytes past
+        for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb + 16);
         for (int p = 0; p < 3; ++p) I.rho[p] = cv.take(2 * I.N * cb);
         I.cot = (double*)cv.take(sizeof(double) * c.nx * c.ny);
         I.hcol = cv.take(cb * c.nx * c.ny);
@@ -212,6 +213,29 @@ struct lbm_handle {
 
 namespace {
 
+// dynamic shared memory of the fused kernel: the staged pull of one plane
+template <class S>
+constexpr size_t stage_bytes(int nt) {
+    return sizeof(typename S::E) == 4 ? (size_t)38 * nt * 4 : 0;
+}
+
+template <class S, int TX, int TY>
+lbm_status prepare_one() {
+    const size_t dyn = stage_bytes<S>(TX * TY);
+    if (dyn > 0)
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    return LBM_OK;
+}
+
+// per-kernel attributes, set once before any launch or capture
+template <class S>
+lbm_status prepare_fused() {
+    lbm_status st = prepare_one<S, 32, 8>();
+    if (st == LBM_OK) st = prepare_one<S, 64, 4>();
+    if (st == LBM_OK) st = prepare_one<S, 32, 4>();
+    return st;
+}
+
 template <class S>
 lbm_status launch_fused(lbm_handle* h) {
     const Shape& sh = SHAPES[h->shape];
@@ -219,13 +243,11 @@ lbm_status launch_fused(lbm_handle* h) {
     const InstDev* in = h->L.d_inst;
     const TileDesc* td = h->L.d_tiles;
     if (sh.tx == 32 && sh.ty == 8)
-        k_stream_collide<S, 32, 8><<<nb, 256, 0, h->stream>>>(in, td, h->L.glob);
+        k_stream_collide<S, 32, 8><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
     else if (sh.tx == 64 && sh.ty == 4)
-        k_stream_collide<S, 64, 4><<<nb, 256, 0, h->stream>>>(in, td, h->L.glob);
+        k_stream_collide<S, 64, 4><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
     else if (sh.tx == 32 && sh.ty == 4)
-        k_stream_collide<S, 32, 4><<<nb, 128, 0, h->stream>>>(in, td, h->L.glob);
-    else if constexpr (sizeof(typename S::T) == 4)
-        k_stream_collide<S, 64, 8><<<nb, 512, 0, h->stream>>>(in, td, h->L.glob);
+        k_stream_collide<S, 32, 4><<<nb, 128, stage_bytes<S>(128), h->stream>>>(in, td, h->L.glob);
     else
         return LBM_EINVAL;
     CK(cudaGetLastError());
@@ -698,6 +720,13 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
     }
     st = upload_tables(h);
     if (st != LBM_OK) return fail(st);
+    switch (h->prec) {
+        case LBM_FP64: st = prepare_fused<StoreF64>(); break;
+        case LBM_FP32: st = prepare_fused<StoreF32>(); break;
+        case LBM_FP16_SHIFTED: st = prepare_fused<StoreF16>(); break;
+        default: st = prepare_fused<StoreB16>(); break;
+    }
+    if (st != LBM_OK) return fail(st);
     for (int k = 0; k < n; ++k) {
         st = init_any(h, k);
         if (st != LBM_OK) return fail(st);
@@ -871,7 +900,6 @@ lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, dou
     int best = -1;
     double bt = 1e300;
     for (int k = 0; k < NSHAPES; ++k) {
-        if (h->prec == LBM_FP64 && SHAPES[k].tx * SHAPES[k].ty > 256) continue;
         lbm_status st = set_shape(h, k);
         if (st != LBM_OK) return st;
         double f = 0, s = 0;
