@@ -56,17 +56,27 @@ __device__ T colour_ext(const InstDev& I, const T* __restrict__ rho, int x, int 
 // ---------------------------------------------------------------------------
 // Fused time step over one tile (TX x TY columns, planes z0..z1-1), marching
 // upwards in z.  Shared memory holds a 3-plane ring of C with a 2-cell halo,
-// a 3-plane ring of unit normals with a 1-cell halo, the core gradient of the
-// next two planes, and a 3-plane ring of moment accumulators with a 1-cell
-// halo into which every stored population is pushed to the node it streams
-// to next step.  Fully interior nodes are stored plainly; tile-edge and halo
-// nodes are added atomically (their buffer was zeroed one step earlier).
+// a 3-plane ring of unit normals with a 1-cell halo and the core gradient of
+// the next two planes.  Every stored population is pushed to the node it
+// streams to next step: a warp is one row of the tile, so the x-neighbour's
+// share moves by a lane shuffle, the share of the planes above and below
+// waits in the thread's registers, and only the sum over the three source
+// rows goes through shared memory (plain stores, no shared atomics).  Fully
+// interior nodes are stored plainly; tile-edge and halo nodes are added
+// atomically (their buffer was zeroed one step earlier).
 // Per plane z, separated by barriers:
 //   1. issue the 38 pull loads of plane z (consumed in 3), flush plane z-2,
 //      store the prefetched C of plane z+2, prefetch C of plane z+3
 //   2. gradient and normals of plane z+1
 //   3. decode the pulled pairs, collide, recolour, evaporate, store, push
 // ---------------------------------------------------------------------------
+// slot of a push that leaves the tile sideways, by its (c_y, c_z); |c_y| + |c_z| <= 1
+__host__ __device__ constexpr int side_slot(int dy, int dz) {
+    return dz == 0 ? (dy == 0 ? 0 : (dy > 0 ? 1 : 2)) : (dz > 0 ? 3 : 4);
+}
+__host__ __device__ constexpr int slot_dy(int k) { return k == 1 ? 1 : (k == 2 ? -1 : 0); }
+__host__ __device__ constexpr int slot_dz(int k) { return k == 3 ? 1 : (k == 4 ? -1 : 0); }
+
 __device__ __forceinline__ int wrap_near(int a, int n) {
     while (a < 0) a += n;
     while (a >= n) a -= n;
@@ -152,14 +162,19 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                      StepGlobals* __restrict__ glob) {
     using T = typename S::T;
     using E = typename S::E;
+    static_assert(TX == 32, "a warp is one row of the tile");
     constexpr int NT = TX * TY;
     constexpr int HX2 = TX + 4, HY2 = TY + 4, HX1 = TX + 2, HY1 = TY + 2;
+    static_assert(NT >= 2 * TX + 2 * HY1, "one thread per halo slot of the flush");
     constexpr int NPF = (HX2 * HY2 + NT - 1) / NT;  // C-halo slots per thread
     __shared__ T sC[3][HY2][HX2];
     using V4 = typename Vec4<T>::type;
     __shared__ V4 sN[3][HY1][HX1];
     __shared__ V4 sG[2][TY][TX];
-    __shared__ T sA[3][2][HY1][HX1];  // component outer: conflict-free pushes
+    // next-step moments of one plane by source row offset: [c_y + 1][comp][row + 1][x]
+    __shared__ T sB[3][2][HY1][TX];
+    // pushes that leave the tile sideways: [source plane ring][left/right][slot][comp][row]
+    __shared__ T sE[3][2][5][2][TY];
     __shared__ double sRed[NT / 32][3];
     __shared__ int sErr;
     // pulled populations of the next plane, staged by asynchronous 4-byte copies
@@ -194,6 +209,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const bool active = tx < tw && ty < th;
+    const unsigned lanes = __ballot_sync(0xffffffffu, active);  // a prefix of the row
     const int x = x0 + tx, y = y0 + ty;
 
     const T rho0 = (T)Ig.rho0, itR = T(1) / (T)Ig.tau_R, itB = T(1) / (T)Ig.tau_B;
@@ -230,7 +246,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
 
     const T hcol = (evap_on && active) ? hcolm[y * nx + x] : T(0);
 
-    for (int s = tid; s < 3 * 2 * HY1 * HX1; s += NT) (&sA[0][0][0][0])[s] = T(0);
+    for (int s = tid; s < 3 * 2 * HY1 * TX; s += NT) (&sB[0][0][0][0])[s] = T(0);
     if (tid == 0) sErr = 0;
 
     // C of plane p into the ring over the tile plus 2 cells (synchronous form)
@@ -245,79 +261,102 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             sC[r][sy][sx] = p < 0 ? ghost(gx, gy) : colour((unsigned)pz * nxy + (unsigned)gy * nx + gx);
         }
     };
-    // prefetched form for planes p >= 0: raw moments into registers now, colour into the ring later
+    // prefetched form for planes p >= 0: raw moments into registers now, colour into the ring later;
+    // slot tid + k NT of the ring plane has the same in-plane source offset on every plane
+    unsigned pfo[NPF];
+#pragma unroll
+    for (int k = 0; k < NPF; ++k) {
+        const int s = tid + k * NT;
+        const int sy = s / HX2, sx = s - sy * HX2;
+        pfo[k] = ~0u;
+        if (s < HX2 * HY2 && sx <= tw + 3 && sy <= th + 3)
+            pfo[k] = (unsigned)wrap_near(y0 - 2 + sy, ny) * nx + wrap_near(x0 - 2 + sx, nx);
+    }
     T pfa[NPF], pfb[NPF];
     int pfp = -100;
     auto prefetchC = [&](int p) {
         pfp = p;
         if (p < 0 || p > nz) return;
-        const int pz = p >= nz ? nz - 1 : p;
+        const unsigned pb = (unsigned)(p >= nz ? nz - 1 : p) * nxy;
 #pragma unroll
         for (int k = 0; k < NPF; ++k) {
-            const int s = tid + k * NT;
-            const int sy = s / HX2, sx = s - sy * HX2;
             pfa[k] = T(1);
             pfb[k] = T(0);
-            if (s < HX2 * HY2 && sx <= tw + 3 && sy <= th + 3) {
-                const int gx = wrap_near(x0 - 2 + sx, nx), gy = wrap_near(y0 - 2 + sy, ny);
-                const unsigned n = (unsigned)pz * nxy + (unsigned)gy * nx + gx;
-                pfa[k] = rho_r[n];
-                pfb[k] = rho_r[N + n];
+            if (pfo[k] != ~0u) {
+                pfa[k] = rho_r[pb + pfo[k]];
+                pfb[k] = rho_r[N + pb + pfo[k]];
             }
         }
     };
     auto commitC = [&]() {
         if (pfp < 0 || pfp > nz) return;
-        const int r = ring(pfp);
+        T* ringp = &sC[ring(pfp)][0][0];
 #pragma unroll
-        for (int k = 0; k < NPF; ++k) {
-            const int s = tid + k * NT;
-            const int sy = s / HX2, sx = s - sy * HX2;
-            if (s < HX2 * HY2 && sx <= tw + 3 && sy <= th + 3)
-                sC[r][sy][sx] = qdiv<T>(pfa[k] - pfb[k], pfa[k] + pfb[k]);
-        }
+        for (int k = 0; k < NPF; ++k)
+            if (pfo[k] != ~0u) ringp[tid + k * NT] = qdiv<T>(pfa[k] - pfb[k], pfa[k] + pfb[k]);
     };
-    // gradient and unit normal of plane q over the tile plus 1 cell
+    // gradient and unit normal of plane q over the tile plus 1 cell: every thread
+    // takes its own node, the first 2 HX1 + 2 TY threads one node of the ring around
+    // the tile as well (slots as indices into a [HY1][HX1] plane)
+    static_assert(NT >= 2 * HX1 + 2 * TY, "one thread per ring node of the normals");
+    int nring = -1;
+    {
+        int sx = -1, sy = -1;
+        if (tid < HX1) {
+            sx = tid, sy = 0;
+        } else if (tid < 2 * HX1) {
+            sx = tid - HX1, sy = th + 1;
+        } else if (tid < 2 * HX1 + TY) {
+            sx = 0, sy = 1 + tid - 2 * HX1;
+        } else if (tid < 2 * HX1 + 2 * TY) {
+            sx = tw + 1, sy = 1 + tid - 2 * HX1 - TY;
+        }
+        if (sx >= 0 && sx <= tw + 1 && sy <= th + 1) nring = sy * HX1 + sx;
+    }
+    auto normal_at = [&](int rm, int r0, int rp, int sy, int sx, T& gx, T& gy, T& gz) {
+        gx = gy = gz = T(0);
+        static_for<1, 19>([&](auto I_) {
+            constexpr int i = decltype(I_)::value;
+            const int rr = cz(i) < 0 ? rm : (cz(i) > 0 ? rp : r0);
+            const T c = sC[rr][sy + 1 + cy(i)][sx + 1 + cx(i)];
+            constexpr T w = (T)wq(i);
+            if constexpr (cx(i) != 0) gx += w * cx(i) * c;
+            if constexpr (cy(i) != 0) gy += w * cy(i) * c;
+            if constexpr (cz(i) != 0) gz += w * cz(i) * c;
+        });
+        gx *= T(3);
+        gy *= T(3);
+        gz *= T(3);
+        const T g2 = gx * gx + gy * gy + gz * gz;
+        V4 nn;
+        if (g2 > T(1e-16)) {
+            const T ig = inv_norm<T>(g2);
+            nn.x = gx * ig;
+            nn.y = gy * ig;
+            nn.z = gz * ig;
+        } else {
+            nn.x = nn.y = nn.z = T(0);
+        }
+        nn.w = T(0);
+        return nn;
+    };
     auto computeN = [&](int q) {
         const int rq = ring(q);
         if (q >= 0 && q < nz) {
             const int rm = ring(q - 1), r0 = ring(q), rp = ring(q + 1);
-            for (int s = tid; s < HX1 * HY1; s += NT) {
-                const int sy = s / HX1, sx = s - sy * HX1;
-                if (sx > tw + 1 || sy > th + 1) continue;
-                T gx = 0, gy = 0, gz = 0;
-                static_for<1, 19>([&](auto I_) {
-                    constexpr int i = decltype(I_)::value;
-                    const int rr = cz(i) < 0 ? rm : (cz(i) > 0 ? rp : r0);
-                    const T c = sC[rr][sy + 1 + cy(i)][sx + 1 + cx(i)];
-                    constexpr T w = (T)wq(i);
-                    if constexpr (cx(i) != 0) gx += w * cx(i) * c;
-                    if constexpr (cy(i) != 0) gy += w * cy(i) * c;
-                    if constexpr (cz(i) != 0) gz += w * cz(i) * c;
-                });
-                gx *= T(3);
-                gy *= T(3);
-                gz *= T(3);
-                const T g2 = gx * gx + gy * gy + gz * gz;
-                V4 nn;
-                if (g2 > T(1e-16)) {
-                    const T ig = inv_norm<T>(g2);
-                    nn.x = gx * ig;
-                    nn.y = gy * ig;
-                    nn.z = gz * ig;
-                } else {
-                    nn.x = nn.y = nn.z = T(0);
-                }
-                nn.w = T(0);
-                sN[rq][sy][sx] = nn;
-                if (sx >= 1 && sx <= tw && sy >= 1 && sy <= th) {
-                    V4 G;
-                    G.x = gx;
-                    G.y = gy;
-                    G.z = gz;
-                    G.w = T(0);
-                    sG[q & 1][sy - 1][sx - 1] = G;
-                }
+            T gx, gy, gz;
+            if (active) {
+                sN[rq][ty + 1][tx + 1] = normal_at(rm, r0, rp, ty + 1, tx + 1, gx, gy, gz);
+                V4 G;
+                G.x = gx;
+                G.y = gy;
+                G.z = gz;
+                G.w = T(0);
+                sG[q & 1][ty][tx] = G;
+            }
+            if (nring >= 0) {
+                const int sy = nring / HX1, sx = nring - sy * HX1;
+                (&sN[rq][0][0])[nring] = normal_at(rm, r0, rp, sy, sx, gx, gy, gz);
             }
         } else if (q == -1 || q == nz) {
             // outside the fluid the normal copies the nearest fluid plane
@@ -330,21 +369,31 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     T evap_sum = 0, top_in = 0, top_out = 0;
     int err = 0;
 
-    // flush the completed accumulator plane q to global memory
+    // next-step moment shares of this thread's column for planes z-1 and z: [c_y + 1][comp]
+    T acm[3][2], ac0[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) acm[d][0] = acm[d][1] = ac0[d][0] = ac0[d][1] = T(0);
+
+    // in-plane offset of this thread's halo node in the flush (halo rows, then halo columns)
+    unsigned hoff = ~0u;
+    if (tid < 2 * TX) {
+        const int side = tid / TX, hx = tid - side * TX;
+        if (hx < tw) hoff = (unsigned)wrap_near(side ? y0 + th : y0 - 1, ny) * nx + (x0 + hx);
+    } else if (tid < 2 * TX + 2 * HY1) {
+        const int k2 = tid - 2 * TX;
+        const int side = k2 / HY1, sy = k2 - side * HY1;
+        if (sy <= th + 1)
+            hoff = (unsigned)wrap_near(y0 - 1 + sy, ny) * nx + wrap_near(side ? x0 + tw : x0 - 1, nx);
+    }
+    // flush the completed plane q (its row shares are in sB) to global memory
     auto flush = [&](int q) {
-        if (q < z0 - 1) return;  // nothing was pushed below the halo plane
-        const int r = ring(q);
-        for (int s = tid; s < HX1 * HY1; s += NT) {
-            const int sy = s / HX1, sx = s - sy * HX1;
-            if (sx > tw + 1 || sy > th + 1) continue;
-            const T a0 = sA[r][0][sy][sx], a1 = sA[r][1][sy][sx];
-            sA[r][0][sy][sx] = T(0);
-            sA[r][1][sy][sx] = T(0);
-            if (q < 0 || q >= nz) continue;
-            const int gx = wrap_near(x0 - 1 + sx, nx), gy = wrap_near(y0 - 1 + sy, ny);
-            const unsigned n = (unsigned)q * nxy + (unsigned)gy * nx + gx;
-            const bool core = sx >= 1 && sx <= tw && sy >= 1 && sy <= th && q >= z0 && q < z1;
-            const bool interior = core && sx > 1 && sx < tw && sy > 1 && sy < th &&
+        if (q < z0 - 1 || q < 0 || q >= nz) return;  // nothing was pushed below the halo plane
+        const bool own = q >= z0 && q < z1;
+        if (active) {
+            const T a0 = sB[0][0][ty + 1][tx] + sB[1][0][ty + 1][tx] + sB[2][0][ty + 1][tx];
+            const T a1 = sB[0][1][ty + 1][tx] + sB[1][1][ty + 1][tx] + sB[2][1][ty + 1][tx];
+            const unsigned n = (unsigned)q * nxy + (unsigned)y * nx + x;
+            const bool interior = own && tx > 0 && tx < tw - 1 && ty > 0 && ty < th - 1 &&
                                   !(q == z0 && z0 > 0) && !(q == z1 - 1 && z1 < nz);
             if (interior) {
                 rho_w[n] = a0;
@@ -352,11 +401,58 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             } else {
                 atomicAdd(rho_w + n, a0);
                 atomicAdd(rho_w + N + n, a1);
-                if (core) {
+                if (own) {
                     rho_z[n] = T(0);
                     rho_z[N + n] = T(0);
                 }
             }
+        }
+        if (tid < 2 * TX) {
+            // halo rows y0-1 and y0+th: only row 0 pushes down, only row th-1 up
+            const int side = tid / TX, hx = tid - side * TX;
+            if (hoff != ~0u) {
+                const T a0 = side ? sB[2][0][th + 1][hx] : sB[0][0][0][hx];
+                const T a1 = side ? sB[2][1][th + 1][hx] : sB[0][1][0][hx];
+                const unsigned n = (unsigned)q * nxy + hoff;
+                atomicAdd(rho_w + n, a0);
+                atomicAdd(rho_w + N + n, a1);
+            }
+        } else if (tid < 2 * TX + 2 * HY1) {
+            // halo columns x0-1 and x0+tw: sideways pushes of the edge lanes, planes q-1..q+1
+            const int k2 = tid - 2 * TX;
+            const int side = k2 / HY1, sy = k2 - side * HY1;
+            if (hoff != ~0u) {
+                T a0 = 0, a1 = 0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int ys = sy - 1 - slot_dy(k), sp = q - slot_dz(k);
+                    if (ys >= 0 && ys < th && sp >= z0 && sp < z1) {
+                        const int r = ring(sp);
+                        a0 += sE[r][side][k][0][ys];
+                        a1 += sE[r][side][k][1][ys];
+                    }
+                }
+                const unsigned n = (unsigned)q * nxy + hoff;
+                atomicAdd(rho_w + n, a0);
+                atomicAdd(rho_w + N + n, a1);
+            }
+        }
+    };
+    // hand the completed share of plane z-1 to the row reduction, then move the shares up one plane
+    auto retire = [&](T (&up)[3][2]) {
+        if (active) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                sB[d][0][ty + d][tx] = acm[d][0];
+                sB[d][1][ty + d][tx] = acm[d][1];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            acm[d][0] = ac0[d][0];
+            acm[d][1] = ac0[d][1];
+            ac0[d][0] = up[d][0];
+            ac0[d][1] = up[d][1];
         }
     };
 
@@ -442,6 +538,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         computeN(z + 1);
         __syncthreads();
         // ---- phase 3: decode, collide, recolour, evaporate, store, push ----
+        T ac1[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};  // shares of plane z+1
         if (active) {
             T Fi[19];
             T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
@@ -556,17 +653,41 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 }
                 T rq, bq;
                 S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
-                const int tz = z + cz(i);
-                T* a;
-                if (tz < 0 || (tz >= nz && top_bc == 0))
-                    a = &sA[rz[1]][0][ty + 1][tx + 1];  // bounces back to this node
-                else if (tz < nz)
-                    a = &sA[rz[cz(i) + 1]][0][ty + 1 + cy(i)][tx + 1 + cx(i)];
-                else
-                    a = nullptr;
-                if (a) {
-                    atomicAdd(a, rq);
-                    atomicAdd(a + HY1 * HX1, bq);
+                const int tz = z + cz(i);  // the same for the whole block
+                if (tz < 0 || (tz >= nz && top_bc == 0)) {
+                    ac0[1][0] += rq;  // bounces back to this node
+                    ac0[1][1] += bq;
+                } else if (tz < nz) {
+                    constexpr int d = cy(i) + 1;
+                    T vr = rq, vb = bq;
+                    if constexpr (cx(i) != 0) {
+                        // the share for this lane's column comes from the lane at x - c_x;
+                        // the edge lane's own share leaves the tile sideways
+                        constexpr int side = cx(i) > 0 ? 1 : 0;
+                        constexpr int k = side_slot(cy(i), cz(i));
+                        if (tx == (side ? tw - 1 : 0)) {
+                            sE[rz[1]][side][k][0][ty] = rq;
+                            sE[rz[1]][side][k][1][ty] = bq;
+                        }
+                        if constexpr (cx(i) > 0) {
+                            vr = __shfl_up_sync(lanes, rq, 1);
+                            vb = __shfl_up_sync(lanes, bq, 1);
+                        } else {
+                            vr = __shfl_down_sync(lanes, rq, 1);
+                            vb = __shfl_down_sync(lanes, bq, 1);
+                        }
+                        if (tx == (side ? 0 : tw - 1)) vr = vb = T(0);  // source outside the tile
+                    }
+                    if constexpr (cz(i) < 0) {
+                        acm[d][0] += vr;
+                        acm[d][1] += vb;
+                    } else if constexpr (cz(i) == 0) {
+                        ac0[d][0] += vr;
+                        ac0[d][1] += vb;
+                    } else {
+                        ac1[d][0] += vr;
+                        ac1[d][1] += vb;
+                    }
                 }
             };
             {  // rest direction
@@ -599,16 +720,24 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     constexpr int i = decltype(I_)::value;
                     if constexpr (cz(i) < 0) inB += (T)wq(i) * rho0;
                 });
-                atomicAdd(&sA[rz[1]][1][ty + 1][tx + 1], inB);
+                ac0[1][1] += inB;
             }
         }
+        retire(ac1);
         if constexpr (ASYNC) issue_pull(z + 1);  // its slots were consumed above by this thread
         __syncthreads();
     }
     if constexpr (ASYNC) cp_async_wait<0>();
-    // the remaining planes touch disjoint ring slots
+    // the last two planes: shares still in registers
+    T none[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     flush(z1 - 2);
+    __syncthreads();
+    retire(none);
+    __syncthreads();
     flush(z1 - 1);
+    __syncthreads();
+    retire(none);
+    __syncthreads();
     flush(z1);
 
     // ---- block sums of the FP64 budgets ----

@@ -23,8 +23,7 @@ namespace {
 struct Shape {
     int tx, ty, chunk;
 };
-const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {64, 4, 0}, {64, 4, 16},
-                        {32, 4, 0}, {32, 4, 16}, {32, 4, 32}, {64, 4, 32}};
+const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {32, 4, 0}, {32, 4, 16}, {32, 4, 32}};
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 64;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
@@ -231,7 +230,6 @@ lbm_status prepare_one() {
 template <class S>
 lbm_status prepare_fused() {
     lbm_status st = prepare_one<S, 32, 8>();
-    if (st == LBM_OK) st = prepare_one<S, 64, 4>();
     if (st == LBM_OK) st = prepare_one<S, 32, 4>();
     return st;
 }
@@ -244,8 +242,6 @@ lbm_status launch_fused(lbm_handle* h) {
     const TileDesc* td = h->L.d_tiles;
     if (sh.tx == 32 && sh.ty == 8)
         k_stream_collide<S, 32, 8><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
-    else if (sh.tx == 64 && sh.ty == 4)
-        k_stream_collide<S, 64, 4><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
     else if (sh.tx == 32 && sh.ty == 4)
         k_stream_collide<S, 32, 4><<<nb, 128, stage_bytes<S>(128), h->stream>>>(in, td, h->L.glob);
     else
@@ -899,8 +895,16 @@ lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, dou
     if (!h || steps_per_candidate < 1) return LBM_EINVAL;
     int best = -1;
     double bt = 1e300;
-    for (int k = 0; k < NSHAPES; ++k) {
+    // tile-edge nodes of the next moment buffer are zeroed by the shape that
+    // wrote the previous one; after a change of shape the moments are rebuilt
+    // from the populations so that the new edges start from zero
+    auto reshape = [&](int k) {
         lbm_status st = set_shape(h, k);
+        for (int i = 0; st == LBM_OK && i < (int)h->cfg.size(); ++i) st = run_moments_any(h, i);
+        return st;
+    };
+    for (int k = 0; k < NSHAPES; ++k) {
+        lbm_status st = reshape(k);
         if (st != LBM_OK) return st;
         double f = 0, s = 0;
         st = lbm_profile_steps(h, 1, &f, &s);  // first launch of this shape: untimed
@@ -911,7 +915,7 @@ lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, dou
             best = k;
         }
     }
-    lbm_status st = set_shape(h, best);
+    lbm_status st = reshape(best);
     if (st != LBM_OK) return st;
     if (chosen) *chosen = best;
     if (best_ms) *best_ms = bt;
