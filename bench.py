@@ -364,6 +364,32 @@ def main():
         del s4
         torch.cuda.empty_cache()
 
+    if not args.no_variants and args.workload == "c2" and args.prec is None:
+        # deposit analysis of Sec. II.B on the c5 wire load (16,000 beads): Kirchhoff network
+        # (FP64 CG, one block) and the axial profiles; synchronous calls, wall-clock timed
+        from paper_2607_06794_b300 import Simulation
+        cfgd, cen, dirs, Xd = workloads.deposit_c5()
+        sd = Simulation([cfgd])
+        sd.add_nanowires(0, len(cen), 8 * cfgd.d0, cen, dirs)
+        sd.write(0, "bead_x", Xd)
+        sd.conductivity(0)
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            cond = sd.conductivity(0)
+        t_cond = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sd.profiles(0, 0, 100.0, 412.0, 52, 127.5, 19.0)
+        t_prof = (time.perf_counter() - t0) / reps
+        variants["deposit_analysis_c5"] = {
+            "beads": int(sd.nb[0]), "edges": cond["n_edges"], "kappa": round(cond["kappa"], 6),
+            "cg_iterations": cond["iterations"], "conductivity_ms": round(t_cond * 1e3, 3),
+            "profiles_ms": round(t_prof * 1e3, 3), "timing": "wall clock of the synchronous call"}
+        sd.close()
+        del sd
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)

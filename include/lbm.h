@@ -122,7 +122,11 @@ enum {
     LBM_FIELD_ACCUM = 8,       /* [6]: step, h0, evaporated, top_in, top_out, n_beads (rw) */
     LBM_FIELD_FEXT = 9,        /* [nz][ny][nx][3]: force the beads put on the fluid in
                                   the last step (r; zero where no bead is near) */
-    LBM_FIELD_THETA_COT = 10   /* [ny][nx]: cot(theta) of the substrate (r) */
+    LBM_FIELD_THETA_COT = 10,  /* [ny][nx]: cot(theta) of the substrate (r) */
+    LBM_FIELD_BEAD_POTENTIAL = 11, /* [n_beads]: node potentials V of the last
+                                      lbm_deposit_conductivity() call (r) */
+    LBM_FIELD_BEAD_CURRENT = 12    /* [n_beads]: node currents I_i* = I_i / I_ref
+                                      (Eqs. (15), (17)) of the same call (r) */
 };
 
 typedef struct lbm_handle lbm_handle;
@@ -190,6 +194,50 @@ lbm_status lbm_write_fields(lbm_handle* h, int inst, unsigned field, const void*
  * clusters, percolation between the electrodes, plus mass budgets.
  * Synchronises the stream. */
 lbm_status lbm_deposit_descriptors(lbm_handle* h, int inst, lbm_descriptors* out);
+
+/* Electrical network of the deposit (Sec. II.B, Eqs. (15)-(18)).
+ * Nodes are the beads; edges are the bonds and the pairs closer than rcon
+ * (the contact graph of lbm_deposit_descriptors, minimum image in x and y),
+ * each with conductance G_ij = 1 / r_ij.  With Delta V = 1, beads with
+ * x < x_src are held at V = 1 and beads with x > x_snk at V = 0; Kirchhoff's
+ * current law fixes the other potentials, solved on the GPU by Jacobi-
+ * preconditioned conjugate gradients in FP64 until ||r|| <= tol ||b||.
+ * Nodes of a component that touches no electrode keep V = 0 and carry no
+ * current.  I_ref = 1 / (x_snk - x_src), the current of a straight filament
+ * of conductance 1/r per unit length spanning the electrodes. */
+typedef struct {
+    double kappa;    /* kappa* = I_tot / I_ref (Eq. (18), one run) */
+    double I_tot;    /* current leaving the source electrode */
+    double I_sink;   /* current entering the sink electrode (= I_tot once converged) */
+    double I_ref;    /* reference current (Eq. (16)) */
+    double residual; /* ||r|| / ||b|| at exit (0 when no free node touches an electrode) */
+    int iterations;  /* conjugate-gradient iterations taken */
+    int n_src;       /* beads held at V = 1 */
+    int n_snk;       /* beads held at V = 0 */
+    int n_edges;     /* edges of the network */
+} lbm_conductivity;
+
+/* Solve the network of instance `inst` (tol > 0; max_iter >= 1 iterations at
+ * most).  Node potentials and currents are then readable as
+ * LBM_FIELD_BEAD_POTENTIAL / LBM_FIELD_BEAD_CURRENT.  Returns LBM_ETIMEOUT,
+ * with the partial result written, when max_iter is reached first, and
+ * LBM_ECAPACITY when the contact graph overflows its 8 edges per bead.
+ * Synchronises the stream. */
+lbm_status lbm_deposit_conductivity(lbm_handle* h, int inst, double tol, int max_iter,
+                                    lbm_conductivity* out);
+
+/* Axial or transverse profiles of the deposit (Sec. II.B, Eqs. (13)-(14)).
+ * axis 0: nbins equal bins along x over [lo, hi), counting only what lies in
+ * the strip |y - centre| <= half_width; axis 1: bins along y, strip in x.
+ * S_x[b] = mean of 2 cos^2(zeta_x) - 1 over the bonds whose midpoint (nearest
+ * image) falls in bin b, 0 for a bin without bonds (Eq. (13));
+ * g[b] = N_b / mean_b N_b with N_b the bead centres in bin b (Eq. (14), equal
+ * bins), 0 everywhere when no bead is counted.  Host outputs of nbins
+ * entries (n_bonds, n_beads may be NULL); 1 <= nbins <= 65536, hi > lo,
+ * half_width >= 0.  Synchronises the stream. */
+lbm_status lbm_deposit_profiles(lbm_handle* h, int inst, int axis, double lo, double hi, int nbins,
+                                double centre, double half_width, double* S_x, double* g,
+                                int* n_bonds, int* n_beads);
 
 /* Release the handle (the workspace stays the caller's). */
 lbm_status lbm_destroy(lbm_handle* h);

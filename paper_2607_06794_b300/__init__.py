@@ -24,7 +24,8 @@ PRECISIONS = {"fp64": _lib.FP64, "fp32": _lib.FP32, "fp16": _lib.FP16_SHIFTED,
 FIELDS = {"populations": _lib.FIELD_POPULATIONS, "moments": _lib.FIELD_MOMENTS,
           "colour": _lib.FIELD_COLOUR, "bead_x": _lib.FIELD_BEAD_X, "bead_v": _lib.FIELD_BEAD_V,
           "bead_f": _lib.FIELD_BEAD_F, "bead_topo": _lib.FIELD_BEAD_TOPO,
-          "accum": _lib.FIELD_ACCUM, "fext": _lib.FIELD_FEXT, "cot": _lib.FIELD_THETA_COT}
+          "accum": _lib.FIELD_ACCUM, "fext": _lib.FIELD_FEXT, "cot": _lib.FIELD_THETA_COT,
+          "bead_potential": _lib.FIELD_BEAD_POTENTIAL, "bead_current": _lib.FIELD_BEAD_CURRENT}
 
 
 class LBMError(RuntimeError):
@@ -181,6 +182,7 @@ class Simulation:
             "bead_f": ((nb, 3), np.float64), "bead_topo": ((nb, 2), np.int32),
             "accum": ((6,), np.float64), "fext": ((c.nz, c.ny, c.nx, 3), np.float64),
             "cot": ((c.ny, c.nx), np.float64),
+            "bead_potential": ((nb,), np.float64), "bead_current": ((nb,), np.float64),
         }[field]
 
     def read(self, inst, field, out=None):
@@ -214,6 +216,28 @@ class Simulation:
         d = _lib.lbm_descriptors()
         _check(self.L.lbm_deposit_descriptors(self.h, inst, C.byref(d)), "lbm_deposit_descriptors")
         return {k: getattr(d, k) for k, _ in _lib.lbm_descriptors._fields_}
+
+    def conductivity(self, inst, tol=1e-12, max_iter=200000) -> dict:
+        """Kirchhoff network of the deposit (kappa*, currents); potentials and node
+        currents are then readable as the 'bead_potential' / 'bead_current' fields."""
+        d = _lib.lbm_conductivity()
+        _check(self.L.lbm_deposit_conductivity(self.h, inst, tol, max_iter, C.byref(d)),
+               "lbm_deposit_conductivity")
+        return {k: getattr(d, k) for k, _ in _lib.lbm_conductivity._fields_}
+
+    def profiles(self, inst, axis, lo, hi, nbins, centre, half_width):
+        """Per-bin S_x^b and g^b (axis 0: bins along x, strip in y; axis 1: the reverse);
+        returns (S_x, g, bond counts, bead counts)."""
+        S = np.zeros(nbins)
+        g = np.zeros(nbins)
+        nb = np.zeros(nbins, np.int32)
+        nd = np.zeros(nbins, np.int32)
+        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+        _check(self.L.lbm_deposit_profiles(self.h, inst, axis, lo, hi, nbins, centre, half_width,
+                                           S.ctypes.data_as(dp), g.ctypes.data_as(dp),
+                                           nb.ctypes.data_as(ip), nd.ctypes.data_as(ip)),
+               "lbm_deposit_profiles")
+        return S, g, nb, nd
 
     def close(self):
         if getattr(self, "h", None):

@@ -11,14 +11,15 @@ OK, EINVAL, ENOMEM_WS, ECUDA, ENAN, EFENE, EBEAD_OOB, ETIMEOUT, ESTATE, ECAPACIT
 FP64, FP32, FP16_SHIFTED, BF16_SHIFTED = range(4)
 # field ids
 (FIELD_POPULATIONS, FIELD_MOMENTS, FIELD_COLOUR, FIELD_BEAD_X, FIELD_BEAD_V, FIELD_BEAD_F,
- FIELD_BEAD_TOPO, FIELD_ACCUM, FIELD_FEXT, FIELD_THETA_COT) = range(1, 11)
+ FIELD_BEAD_TOPO, FIELD_ACCUM, FIELD_FEXT, FIELD_THETA_COT, FIELD_BEAD_POTENTIAL,
+ FIELD_BEAD_CURRENT) = range(1, 13)
 
 # every entry point that include/lbm.h declares
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_substrate_pattern", "lbm_add_nanowires",
            "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
            "lbm_deposit_descriptors", "lbm_destroy", "lbm_status_string", "lbm_mlp_param_count",
            "lbm_mlp_scratch_bytes", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
-           "lbm_deposit_descriptors_noalloc")
+           "lbm_deposit_descriptors_noalloc", "lbm_deposit_conductivity", "lbm_deposit_profiles")
 
 
 class lbm_config(C.Structure):
@@ -47,6 +48,14 @@ class lbm_descriptors(C.Structure):
     ]
 
 
+class lbm_conductivity(C.Structure):
+    _fields_ = [
+        ("kappa", C.c_double), ("I_tot", C.c_double), ("I_sink", C.c_double), ("I_ref", C.c_double),
+        ("residual", C.c_double), ("iterations", C.c_int), ("n_src", C.c_int), ("n_snk", C.c_int),
+        ("n_edges", C.c_int),
+    ]
+
+
 _lib = None
 
 
@@ -58,7 +67,7 @@ def load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"liblbm.so not built at {LIB_PATH}; run paper_2607_06794_b300/build.py")
     L = C.CDLL(LIB_PATH)
-    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
     L.lbm_workspace_bytes.restype = C.c_size_t
     L.lbm_workspace_bytes.argtypes = [C.POINTER(lbm_config), C.c_int]
     L.lbm_create.restype = C.c_int
@@ -100,6 +109,11 @@ def load():
     L.lbm_deposit_descriptors_noalloc.restype = C.c_int
     L.lbm_deposit_descriptors_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                                   C.c_double, C.c_double, vp, vp]
+    L.lbm_deposit_conductivity.restype = C.c_int
+    L.lbm_deposit_conductivity.argtypes = [vp, C.c_int, C.c_double, C.c_int, C.POINTER(lbm_conductivity)]
+    L.lbm_deposit_profiles.restype = C.c_int
+    L.lbm_deposit_profiles.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
+                                       C.c_double, dp, dp, ip, ip]
     L.lbm_status_string.restype = C.c_char_p
     L.lbm_status_string.argtypes = [C.c_int]
     _lib = L

@@ -3,6 +3,8 @@
 // time step (captured once into a CUDA graph and replayed), field transfer,
 // nanowire placement and descriptors.
 #include <math.h>
+
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 
@@ -13,6 +15,7 @@
 
 #include "../../include/lbm.h"
 #include "kernels_beads.cuh"
+#include "kernels_network.cuh"
 
 using namespace lbm;
 
@@ -27,6 +30,7 @@ const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {32, 4, 0}, {32, 4
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 64;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
+constexpr int PROFILE_MAX_BINS = 65536;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -153,10 +157,17 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.max_edges = 8 * c.max_beads + 64;
             I.edges = (int2*)cv.take(sizeof(int2) * (size_t)I.max_edges);
             I.nedges = (int*)cv.take(sizeof(int));
+            I.net = (double*)cv.take(sizeof(double) * 6 * (size_t)c.max_beads);
+            I.netout = (double*)cv.take(sizeof(double) * 10);
+            I.csr_row = (int*)cv.take(sizeof(int) * ((size_t)c.max_beads + 1));
+            I.csr_cnt = (int*)cv.take(sizeof(int) * 2 * (size_t)c.max_beads);
+            I.csr_col = (int*)cv.take(sizeof(int) * 2 * (size_t)I.max_edges);
+            I.csr_val = (double*)cv.take(sizeof(double) * 2 * (size_t)I.max_edges);
         }
         need_stage = std::max(need_stage, (size_t)(2 * 19 * I.N * sizeof(double)));
         need_stage = std::max(need_stage, (size_t)(5 * I.N * sizeof(double)));
     }
+    need_stage = std::max(need_stage, (size_t)PROFILE_MAX_BINS * 24);  // deposit profiles
     L.stage_bytes = std::min(need_stage, STAGE_BYTES);
     L.stage = (double*)cv.take(L.stage_bytes);
 }
@@ -948,6 +959,8 @@ static size_t field_bytes(const lbm_config& c, int nb, unsigned f) {
         case LBM_FIELD_ACCUM: return 6 * 8;
         case LBM_FIELD_FEXT: return 3 * N * 8;
         case LBM_FIELD_THETA_COT: return (size_t)c.nx * c.ny * 8;
+        case LBM_FIELD_BEAD_POTENTIAL:
+        case LBM_FIELD_BEAD_CURRENT: return (size_t)nb * 8;
         default: return 0;
     }
 }
@@ -1004,6 +1017,12 @@ lbm_status lbm_read_fields(lbm_handle* h, int inst, unsigned field, void* dst, s
             break;
         }
         case LBM_FIELD_THETA_COT: CK(cudaMemcpy(dst, I.cot, bytes, cudaMemcpyDeviceToHost)); break;
+        case LBM_FIELD_BEAD_POTENTIAL:
+        case LBM_FIELD_BEAD_CURRENT: {
+            const double* p = field == LBM_FIELD_BEAD_POTENTIAL ? I.net : I.net + 5 * (size_t)I.nb_max;
+            CK(cudaMemcpy(dst, p, bytes, cudaMemcpyDeviceToHost));
+            break;
+        }
     }
     if (st != LBM_OK) return st;
     return latched(h);
@@ -1079,6 +1098,68 @@ lbm_status lbm_deposit_descriptors(lbm_handle* h, int inst, lbm_descriptors* out
     out->top_in = a[3];
     out->top_out = a[4];
     out->step = h->step;
+    return latched(h);
+}
+
+lbm_status lbm_deposit_conductivity(lbm_handle* h, int inst, double tol, int max_iter,
+                                    lbm_conductivity* out) {
+    if (!valid_inst(h, inst) || !out || !(tol > 0.0) || max_iter < 1) return LBM_EINVAL;
+    const lbm_config& c = h->cfg[inst];
+    if (!(c.x_snk > c.x_src)) return LBM_EINVAL;
+    const InstDev& I = h->L.inst[inst];
+    memset(out, 0, sizeof(*out));
+    out->I_ref = 1.0 / (c.x_snk - c.x_src);
+    CK(cudaStreamSynchronize(h->stream));
+    if (I.nb_max == 0) return latched(h);
+    CK(cudaMemsetAsync(I.nedges, 0, sizeof(int), h->stream));
+    if (I.nb > 0) k_desc_edges<<<(I.nb + 127) / 128, 128, 0, h->stream>>>(h->L.d_inst, inst);
+    k_net_solve<<<1, NET_THREADS, 0, h->stream>>>(h->L.d_inst, inst, tol, max_iter);
+    CK(cudaGetLastError());
+    double o[10];
+    CK(cudaMemcpyAsync(o, I.netout, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->kappa = o[0];
+    out->I_tot = o[1];
+    out->I_sink = o[2];
+    out->I_ref = o[3];
+    out->residual = o[4];
+    out->iterations = (int)o[5];
+    out->n_src = (int)o[6];
+    out->n_snk = (int)o[7];
+    out->n_edges = (int)o[8];
+    const lbm_status st = latched(h);
+    if (st != LBM_OK) return st;
+    return o[9] != 0.0 ? LBM_OK : LBM_ETIMEOUT;
+}
+
+lbm_status lbm_deposit_profiles(lbm_handle* h, int inst, int axis, double lo, double hi, int nbins,
+                                double centre, double half_width, double* S_x, double* g, int* n_bonds,
+                                int* n_beads) {
+    if (!valid_inst(h, inst) || !S_x || !g || (axis != 0 && axis != 1) || nbins < 1 ||
+        nbins > PROFILE_MAX_BINS || !(hi > lo) || !(half_width >= 0.0) || !std::isfinite(centre))
+        return LBM_EINVAL;
+    const InstDev& I = h->L.inst[inst];
+    CK(cudaStreamSynchronize(h->stream));
+    if (I.nb_max == 0) {
+        for (int k = 0; k < nbins; ++k) {
+            S_x[k] = g[k] = 0.0;
+            if (n_bonds) n_bonds[k] = 0;
+            if (n_beads) n_beads[k] = 0;
+        }
+        return latched(h);
+    }
+    double* Sd = h->L.stage;
+    double* gd = Sd + nbins;
+    int* bd = (int*)(gd + nbins);
+    int* nd = bd + nbins;
+    k_net_profiles<<<1, NET_THREADS, 0, h->stream>>>(h->L.d_inst, inst, axis, lo, hi, nbins, centre, half_width,
+                                                      Sd, gd, bd, nd);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(S_x, Sd, sizeof(double) * nbins, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(g, gd, sizeof(double) * nbins, cudaMemcpyDeviceToHost, h->stream));
+    if (n_bonds) CK(cudaMemcpyAsync(n_bonds, bd, sizeof(int) * nbins, cudaMemcpyDeviceToHost, h->stream));
+    if (n_beads) CK(cudaMemcpyAsync(n_beads, nd, sizeof(int) * nbins, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return latched(h);
 }
 

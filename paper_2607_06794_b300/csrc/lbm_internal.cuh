@@ -221,6 +221,13 @@ struct InstDev {
     int max_edges;
     int pad1;
     double* desc;                // [8] descriptor results
+    // electrical network of the deposit
+    double* net;                 // [6][nb_max]: V, r, p, q, 1/diag, I*
+    double* netout;              // [10] network results
+    int* csr_row;                // [nb_max + 1]
+    int* csr_cnt;                // [2][nb_max]: fill cursors, node classes
+    int* csr_col;                // [2 max_edges]
+    double* csr_val;             // [2 max_edges] conductances
 };
 
 struct StepGlobals {

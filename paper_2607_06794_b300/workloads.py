@@ -118,5 +118,26 @@ def batched_c4(prec="fp16", n=64):
     return Workload(f"c4_batched_{n}_instances", cfgs, ths, ws, 10000)
 
 
+def deposit_c5(seed=7, n_wires=2000, n_beads=8, spread=0.6):
+    """A dried deposit with the c5 wire load for the analysis kernels: 2000 straight
+    filaments of 8 beads lying flat (z = 1) on the 512 x 256 substrate, centres uniform
+    in the droplet's central region, directions scattered by `spread` radians about x,
+    electrodes at x_c -/+ 0.26 (2a) of the aspect-6 cap.  Returns (cfg, centres, dirs, X)
+    with X the bead positions wrapped into the lattice."""
+    g = np.random.default_rng(seed)
+    nx, ny = 512, 256
+    cen = np.c_[g.uniform(100, 412, n_wires), g.uniform(90, 166, n_wires), np.ones(n_wires)]
+    ang = g.normal(0.0, spread, n_wires)
+    dirs = np.c_[np.cos(ang), np.sin(ang), np.zeros(n_wires)]
+    k = np.arange(n_beads) - (n_beads - 1) / 2.0
+    X = (cen[:, None, :] + 2.0 * k[None, :, None] * dirs[:, None, :]).reshape(-1, 3)
+    X[:, 0] %= nx
+    X[:, 1] %= ny
+    c = Config(nx, ny, 8, prec="fp32", cx=255.5, cy=127.5, cz=-0.5, a=200, b=100, c=6.0, width=2.0,
+               theta_deg=90.0, top_bc=1, max_beads=n_wires * n_beads + 64,
+               x_src=255.5 - 0.26 * 384, x_snk=255.5 + 0.26 * 384, seed=seed)
+    return c, cen, dirs, X
+
+
 WORKLOADS = {"c1": droplet_c1, "c2": droplet_c2, "c5": droplet_c5, "paper": paper_droplet,
              "c4": batched_c4}

@@ -57,3 +57,16 @@ def random_filaments(seed, n_fil, n_beads, spacing, box_lo, box_hi, min_dist=2.0
         ds.append(d)
         placed = np.vstack([placed, X])
     return np.array(cs), np.array(ds)
+
+
+def flat_deposit(seed, n_fil, n_beads, box, z=1.0, spread=0.6, spacing=2.0):
+    """A dried deposit: straight filaments lying flat at height z with uniform centres in
+    box = (x0, x1, y0, y1) and directions scattered by `spread` (radians) about the x axis.
+    Returns centres, directions and fil, pos, X of the beads (overlaps allowed)."""
+    g = rng(seed)
+    x0, x1, y0, y1 = box
+    cen = np.c_[g.uniform(x0, x1, n_fil), g.uniform(y0, y1, n_fil), np.full(n_fil, z)]
+    ang = g.normal(0.0, spread, n_fil)
+    dirs = np.c_[np.cos(ang), np.sin(ang), np.zeros(n_fil)]
+    fil, pos, X = straight_filaments(cen, dirs, n_beads, spacing)
+    return cen, dirs, fil, pos, X
