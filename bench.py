@@ -35,11 +35,11 @@ TRAFFIC = {}
 
 
 def kernel_hash():
+    """Hash of the sources of the fused kernel (its file and the shared storage policies)."""
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2607_06794_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("kernels_fluid.cuh", "lbm_internal.cuh"):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 

@@ -44,35 +44,32 @@ __device__ __forceinline__ T pair_dUdr(const InstDev& I, bool same, int sep, T r
     return f;
 }
 
-// trilinear stencil around a position (z clamped into the fluid)
-__device__ __forceinline__ void stencil(const InstDev& I, const double* X, long long* id, double* w) {
-    // a non-finite position (already an error) is mapped to the origin so that
-    // no index is ever formed from it
+// index within one period of a coordinate that left [0, n) by less than n
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ double wrap1(double a, int n) { return a < 0.0 ? a + n : (a >= n ? a - n : a); }
+
+// Corner c (bit 0: x, bit 1: y, bit 2: z) of the trilinear stencil around a
+// position (z clamped into the fluid): node index, weight and 8^3 coupling tile.
+// Positions are kept inside the periodic box by the integrator; a non-finite
+// position (already an error) is mapped to the origin so that no index is
+// ever formed from it.
+template <typename W>
+__device__ __forceinline__ void stencil_corner(const InstDev& I, const double* X, int c, long long& id, W& w,
+                                               int& tile) {
     double px = X[0], py = X[1], pz = X[2];
     if (!(isfinite(px) && isfinite(py) && isfinite(pz))) px = py = pz = 0.0;
-    px -= I.nx * floor(px / I.nx);
-    py -= I.ny * floor(py / I.ny);
+    px = wrap1(px, I.nx);
+    py = wrap1(py, I.ny);
     pz = pz < 0.0 ? 0.0 : (pz > I.nz - 1 ? (double)(I.nz - 1) : pz);
-    const int x0 = min((int)floor(px), I.nx - 1), y0 = min((int)floor(py), I.ny - 1);
+    const int x0 = min(max((int)floor(px), 0), I.nx - 1), y0 = min(max((int)floor(py), 0), I.ny - 1);
     int z0 = (int)floor(pz);
     if (I.nz >= 2 && z0 > I.nz - 2) z0 = I.nz - 2;
     const double fx = px - x0, fy = py - y0, fz = pz - z0;
-    const int z1 = I.nz >= 2 ? z0 + 1 : z0;
-    int k = 0;
-    for (int c = 0; c < 2; ++c)
-        for (int b = 0; b < 2; ++b)
-            for (int a = 0; a < 2; ++a) {
-                const int xx = wrapi(x0 + a, I.nx), yy = wrapi(y0 + b, I.ny), zz = c ? z1 : z0;
-                id[k] = ((long long)zz * I.ny + yy) * I.nx + xx;
-                w[k] = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy) * (c ? fz : 1.0 - fz);
-                ++k;
-            }
-}
-
-__device__ __forceinline__ long long tile_of(const InstDev& I, long long node) {
-    const int x = (int)(node % I.nx), y = (int)((node / I.nx) % I.ny),
-              z = (int)(node / ((long long)I.nx * I.ny));
-    return ((long long)(z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
+    const int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
+    const int xx = wrap1(x0 + a, I.nx), yy = wrap1(y0 + b, I.ny), zz = (e && I.nz >= 2) ? z0 + 1 : z0;
+    id = ((long long)zz * I.ny + yy) * I.nx + xx;
+    w = (W)((a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy) * (e ? fz : 1.0 - fz));
+    tile = ((zz >> 3) * I.t8y + (yy >> 3)) * I.t8x + (xx >> 3);
 }
 
 // cell of a (finite, wrapped) position; cells are at least rlist wide
@@ -84,10 +81,28 @@ __device__ __forceinline__ int cell_of(const InstDev& I, float x, float y, float
     return (cz_ * I.cgy + cy_) * I.cgx + cx_;
 }
 
+// Clear the coupling-tile flags (and the flagged-tile count behind them) and
+// the cell counts of every instance with beads, before the step's bead phase.
+__global__ void k_bead_clear(const InstDev* __restrict__ insts) {
+    const InstDev& I = insts[blockIdx.y];
+    if (I.tflag == nullptr) return;
+    const int nt = I.t8x * I.t8y * I.t8z + 1, nc = I.cgx * I.cgy * I.cgz;
+    const int nw = (int)(I.N >> 5) + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt + nc + nw; i += gridDim.x * blockDim.x) {
+        if (i < nt)
+            I.tflag[i] = 0u;
+        else if (i < nt + nc)
+            I.ccount[i - nt] = 0;
+        else
+            I.nbit[i - nt - nc] = 0u;
+    }
+}
+
 // Step start, one warp per bead: remember the position, keep an FP32 copy
-// for the neighbour search, file the bead in its cell, and flag the coupling
-// tiles its trilinear stencil can reach during the step (lane = one corner of
-// the 4x4x2 reach; duplicates are harmless).
+// for the neighbour search, file the bead in its cell, take the first half
+// kick and drift of the step (FP64, lane 0), and flag the coupling tiles its
+// trilinear stencil can reach during the step (lane = one corner of the 4x4x2
+// reach; duplicates are harmless).
 __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
     const InstDev I = insts[blockIdx.y];
     const int lane = threadIdx.x & 31;
@@ -110,16 +125,35 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
             I.cbeads[(size_t)c * CELL_CAP + slot] = a;
         else
             atomicOr(I.err, ERR_CAP);
+        const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
+        double Y[3];
+        for (int d = 0; d < 3; ++d) {
+            const double vh = I.bv[3 * a + d] + hk * I.bF[3 * a + d];
+            I.bvh[3 * a + d] = vh;
+            Y[d] = X[d] + dt * vh;
+        }
+        Y[0] = wrap1(Y[0], I.nx);
+        Y[1] = wrap1(Y[1], I.ny);
+        if (!(Y[2] > -0.5 && Y[2] < I.nz - 0.5)) atomicOr(I.err, ERR_BEAD);
+        for (int d = 0; d < 3; ++d) I.bx2[3 * a + d] = Y[d];
     }
     const double zc = X[2] < -1.0 ? -1.0 : (X[2] > I.nz ? (double)I.nz : X[2]);
-    const int fx = wrapi((int)floor(X[0]), I.nx), fy = wrapi((int)floor(X[1]), I.ny), fz = (int)floor(zc);
+    const int fx = wrap_near((int)floor(X[0]), I.nx), fy = wrap_near((int)floor(X[1]), I.ny), fz = (int)floor(zc);
     const int dx = (lane & 3) - 1, dy = ((lane >> 2) & 3) - 1, dz = (lane >> 4) ? 2 : -1;
-    const int x = wrapi(fx + dx, I.nx), y = wrapi(fy + dy, I.ny);
+    const int x = wrap_near(fx + dx, I.nx), y = wrap_near(fy + dy, I.ny);
     int z = fz + dz;
     z = z < 0 ? 0 : (z >= I.nz ? I.nz - 1 : z);
     const int t = ((z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
     // most tiles are already flagged by a neighbour: read before the atomic
     if (!((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u) I.tlist[atomicAdd(I.tcount, 1)] = t;
+    // the 4x4x4 nodes the stencil can reach during the step, two per lane
+    for (int k = 0; k < 2; ++k) {
+        const int zr = fz + (lane >> 4) * 2 + k - 1;
+        const int zz = zr < 0 ? 0 : (zr >= I.nz ? I.nz - 1 : zr);
+        const long long node = ((long long)zz * I.ny + y) * I.nx + x;
+        const unsigned bit = 1u << (node & 31);
+        if (!(((volatile unsigned*)I.nbit)[node >> 5] & bit)) atomicOr(I.nbit + (node >> 5), bit);
+    }
 }
 
 // u* = (j + (F_s + body)/2)/rho and grad C on the nodes of flagged tiles.
@@ -155,12 +189,48 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     const int X0 = (t % I.t8x) * 8, Y0 = ((t / I.t8x) % I.t8y) * 8, Z0 = (t / (I.t8x * I.t8y)) * 8;
     const int tid = threadIdx.x;
     __syncthreads();  // shared blocks of the previous tile are free
+    // colour of the planes in the fluid (z = nz copies the top plane), then the
+    // wetting ghost plane z = -1 from the shared plane z = 0 where it holds the
+    // 3x3 neighbourhood, else from memory
     for (int s = tid; s < 12 * 12 * 12; s += 512) {
         const int lx = s % 12, ly = (s / 12) % 12, lz = s / 144;
         const int z = Z0 - 2 + lz;
-        sC[lz][ly][lx] = (z < -1 || z > nz) ? T(0) : colour_ext<T>(I, rho, X0 - 2 + lx, Y0 - 2 + ly, z);
+        T c = T(0);
+        if (z >= 0 && z <= nz) {
+            const int x = wrap_near(X0 - 2 + lx, nx), y = wrap_near(Y0 - 2 + ly, ny);
+            c = colour_of(rho, N, ((long long)(z < nz ? z : nz - 1) * ny + y) * nx + x);
+        }
+        sC[lz][ly][lx] = c;
     }
     __syncthreads();
+    if (Z0 == 0) {
+        for (int s = tid; s < 12 * 12; s += 512) {
+            const int lx = s % 12, ly = s / 12;
+            const int x = wrap_near(X0 - 2 + lx, nx), y = wrap_near(Y0 - 2 + ly, ny);
+            T g;
+            if (lx >= 1 && lx <= 10 && ly >= 1 && ly <= 10) {
+                T ax = 0, ay = 0;
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int k = (dx != 0) + (dy != 0);
+                        const T w = k == 0 ? T(4.0 / 9.0) : (k == 1 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+                        const T c = sC[2][ly + dy][lx + dx];
+                        ax += w * dx * c;
+                        ay += w * dy * c;
+                    }
+                ax *= T(3);
+                ay *= T(3);
+                g = sC[2][ly][lx] + (T)I.cot[y * nx + x] * sqrt(ax * ax + ay * ay);
+                g = g > T(1) ? T(1) : (g < T(-1) ? T(-1) : g);
+            } else {
+                g = ghost_colour<T>(I, rho, x, y);
+            }
+            sC[1][ly][lx] = g;
+        }
+        __syncthreads();
+    }
     for (int s = tid; s < 1000; s += 512) {
         const int lx = s % 10, ly = (s / 10) % 10, lz = s / 100;
         const int z = Z0 - 1 + lz;
@@ -205,6 +275,8 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     // the sub-steps of this step accumulate the drag reaction here from zero
     T* fe = (T*)I.fext + 3 * node;
     fe[0] = fe[1] = fe[2] = T(0);
+    // u* and grad C are read only inside the beads' reach (marked at the step start)
+    if (!((I.nbit[node >> 5] >> (node & 31)) & 1u)) return;
     T gx = 0, gy = 0, gz = 0, kap = 0;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -226,6 +298,7 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     const T hs = T(0.5) * (T)I.sigma;
     const T rho0 = (T)I.rho0;
     T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+    const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx), ym = wrap1(y - 1, ny), yp = wrap1(y + 1, ny);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int sz = z - cz(i);
@@ -236,7 +309,8 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
             r = T(0);
             b = (T)wq(i) * rho0;
         } else {
-            const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
+            const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
+            const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
             S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i), rho0,
                     r, b);
         }
@@ -258,8 +332,12 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     g[2] = gz;
 }
 
-// Verlet neighbour list of the step, one warp per bead: lanes take the entries
-// of the 27 surrounding cells (FP32 positions; the skin absorbs the rounding).
+// Verlet neighbour list of the step, one warp per bead (FP32 positions; the
+// skin absorbs the rounding).  Lanes 0..26 read the counts of the 27 (distinct
+// periodic) neighbour cells at once; the candidates of all cells are then
+// numbered cell by cell and taken 32 at a time, each lane finding its cell by a
+// binary search over the lanes' prefix counts.  The list keeps the cell-major
+// order of a plain cell-by-cell scan.
 __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
     const InstDev I = insts[blockIdx.y];
     const int lane = threadIdx.x & 31;
@@ -273,36 +351,54 @@ __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
     const float r2 = (float)(I.rlist * I.rlist);
     const float Lx = (float)I.nx, Ly = (float)I.ny;
     const int nxo = min(3, I.cgx), nyo = min(3, I.cgy);  // distinct periodic neighbour cells
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
+    // this lane's cell: lane = (dz + 1) * 9 + oy * 3 + ox
+    int cell = 0, m = 0;
+    if (lane < 27) {
+        const int dz = lane / 9 - 1, oy = (lane / 3) % 3, ox = lane % 3;
         const int zz = iz + dz;
-        if (zz < 0 || zz >= I.cgz) continue;
-        for (int oy = 0; oy < nyo; ++oy) {
-            const int yy = wrapi(iy + (nyo == 3 ? oy - 1 : oy), I.cgy);
-            for (int ox = 0; ox < nxo; ++ox) {
-                const int xx = wrapi(ix + (nxo == 3 ? ox - 1 : ox), I.cgx);
-                const int c = (zz * I.cgy + yy) * I.cgx + xx;
-                const int m = min(I.ccount[c], CELL_CAP);
-                bool hit = false;
-                int b = -1;
-                if (lane < m) {
-                    b = I.cbeads[(size_t)c * CELL_CAP + lane];
-                    if (b != a && !(I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2)) {
-                        float ex = I.bxf[3 * b] - xa, ey = I.bxf[3 * b + 1] - ya;
-                        const float ez = I.bxf[3 * b + 2] - za;
-                        ex = ex > 0.5f * Lx ? ex - Lx : (ex < -0.5f * Lx ? ex + Lx : ex);
-                        ey = ey > 0.5f * Ly ? ey - Ly : (ey < -0.5f * Ly ? ey + Ly : ey);
-                        hit = ex * ex + ey * ey + ez * ez < r2;
-                    }
-                }
-                const unsigned msk = __ballot_sync(0xffffffffu, hit);
-                if (hit) {
-                    const int k = cnt + __popc(msk & ((1u << lane) - 1u));
-                    if (k < I.max_nbr) I.nbr[(long long)a * I.max_nbr + k] = b;
-                }
-                cnt += __popc(msk);
+        if (zz >= 0 && zz < I.cgz && oy < nyo && ox < nxo) {
+            const int yy = wrap_near(iy + (nyo == 3 ? oy - 1 : oy), I.cgy);
+            const int xx = wrap_near(ix + (nxo == 3 ? ox - 1 : ox), I.cgx);
+            cell = (zz * I.cgy + yy) * I.cgx + xx;
+            m = min(I.ccount[cell], CELL_CAP);
+        }
+    }
+    int incl = m;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int excl = incl - m;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int cnt = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int k = base + lane;
+        // owner: the last lane whose exclusive prefix is <= k
+        int lo = 0;
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, lo + step);
+            if (lo + step < 32 && e <= k) lo += step;
+        }
+        const int oc = __shfl_sync(0xffffffffu, cell, lo);
+        const int oe = __shfl_sync(0xffffffffu, excl, lo);
+        bool hit = false;
+        int b = -1;
+        if (k < total) {
+            b = I.cbeads[(size_t)oc * CELL_CAP + (k - oe)];
+            if (b != a && !(I.bfil[b] == fa && abs(I.bpos[b] - pa) <= 2)) {
+                float ex = I.bxf[3 * b] - xa, ey = I.bxf[3 * b + 1] - ya;
+                const float ez = I.bxf[3 * b + 2] - za;
+                ex = ex > 0.5f * Lx ? ex - Lx : (ex < -0.5f * Lx ? ex + Lx : ex);
+                ey = ey > 0.5f * Ly ? ey - Ly : (ey < -0.5f * Ly ? ey + Ly : ey);
+                hit = ex * ex + ey * ey + ez * ez < r2;
             }
         }
+        const unsigned msk = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int kk = cnt + __popc(msk & ((1u << lane) - 1u));
+            if (kk < I.max_nbr) I.nbr[(long long)a * I.max_nbr + kk] = b;
+        }
+        cnt += __popc(msk);
     }
     if (lane == 0) {
         if (cnt > I.max_nbr) {
@@ -313,42 +409,33 @@ __global__ void k_bead_nlist(const InstDev* __restrict__ insts) {
     }
 }
 
-// First half kick and drift of the step (FP64 integration)
-__global__ void k_bead_kickdrift(const InstDev* __restrict__ insts) {
-    const InstDev I = insts[blockIdx.y];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= I.nb) return;
-    const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
-    double X[3];
-    for (int d = 0; d < 3; ++d) {
-        const double vh = I.bv[3 * a + d] + hk * I.bF[3 * a + d];
-        I.bvh[3 * a + d] = vh;
-        X[d] = I.bx[3 * a + d] + dt * vh;
-    }
-    X[0] -= I.nx * floor(X[0] / I.nx);
-    X[1] -= I.ny * floor(X[1] / I.ny);
-    if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) atomicOr(I.err, ERR_BEAD);
-    for (int d = 0; d < 3; ++d) I.bx2[3 * a + d] = X[d];
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Force evaluation of sub-step s (1-based), one warp per bead: lanes share the
-// bonded partners and the neighbour list (pair forces in the compute type),
-// lanes 0..7 take one stencil node each for the interpolation of u* and
-// grad C and for the reaction spread; lane 0 adds drag, solvation, adhesion
-// and friction and integrates in FP64 (second half kick; if not last, the next
-// first half kick and drift).
+// sum over the 8 lanes of one bead's group (mask: the group's lanes)
+template <typename T>
+__device__ __forceinline__ T group8_sum(T v, unsigned mask) {
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+// Force evaluation of sub-step s (1-based), eight lanes per bead (four beads
+// per warp): the lanes share the bonded partners and the neighbour list (pair
+// forces in the compute type) and take one stencil node each for the
+// interpolation of u* and grad C and for the reaction spread; the group's
+// first lane adds drag, solvation, adhesion and friction and integrates in
+// FP64 (second half kick; if not last, the next first half kick and drift).
+constexpr int BEAD_LANES = 8;
 template <typename T>
 __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     const InstDev I = insts[blockIdx.y];
-    const int lane = threadIdx.x & 31;
-    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (a >= I.nb) return;
+    const int lane = threadIdx.x & (BEAD_LANES - 1);
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) / BEAD_LANES;
+    if (a >= I.nb) return;  // a whole group leaves together
     const bool last = s == I.substeps;
     const double* cur = (s & 1) ? I.bx2 : I.bx;
     double* nxt = (s & 1) ? I.bx : I.bx2;
@@ -359,7 +446,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     const int nn = I.nnbr[a];
     // ---- pair forces, candidates spread over the lanes ----
     T fx = 0, fy = 0, fz = 0;
-    for (int c = lane; c < 4 + nn; c += 32) {
+    for (int c = lane; c < 4 + nn; c += BEAD_LANES) {
         int b;
         bool same;
         int sep;
@@ -374,8 +461,19 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
             same = I.bfil[b] == fa;
             sep = same ? abs(I.bpos[b] - pa) : 0;
         }
-        const T d0 = (T)min_image(cur[3 * b] - P[0], I.nx), d1 = (T)min_image(cur[3 * b + 1] - P[1], I.ny),
-                d2 = (T)(cur[3 * b + 2] - P[2]);
+        T d0, d1;
+        if constexpr (sizeof(T) == 8) {
+            d0 = (T)min_image(cur[3 * b] - P[0], I.nx);
+            d1 = (T)min_image(cur[3 * b + 1] - P[1], I.ny);
+        } else {
+            // the FP64 difference rounded once, the periodic image taken in FP32
+            d0 = (T)(cur[3 * b] - P[0]);
+            d1 = (T)(cur[3 * b + 1] - P[1]);
+            const T hx = T(0.5) * I.nx, hy = T(0.5) * I.ny;
+            d0 = d0 > hx ? d0 - (T)I.nx : (d0 < -hx ? d0 + (T)I.nx : d0);
+            d1 = d1 > hy ? d1 - (T)I.ny : (d1 < -hy ? d1 + (T)I.ny : d1);
+        }
+        const T d2 = (T)(cur[3 * b + 2] - P[2]);
         const T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         const T g = pair_dUdr<T>(I, same, sep, r, err);
         if (g != T(0)) {
@@ -385,26 +483,27 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
             fz += gr * d2;
         }
     }
-    fx = warp_sum(fx);
-    fy = warp_sum(fy);
-    fz = warp_sum(fz);
+    fx = group8_sum(fx, gmask);
+    fy = group8_sum(fy, gmask);
+    fz = group8_sum(fz, gmask);
     // ---- interpolation of u* and grad C, one stencil node per lane ----
-    long long id[8];
-    double w[8];
-    stencil(I, P, id, w);
-    T u[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
-    if (lane < 8) {
-        const T* ust = (const T*)I.ust + 3 * id[lane];
-        const T* gcl = (const T*)I.gcol + 3 * id[lane];
-        const T wl = (T)w[lane];
+    long long idl = 0;
+    double wdl = 0.0;
+    int tl = 0;
+    stencil_corner(I, P, lane, idl, wdl, tl);
+    T u[3], gc[3];
+    {
+        const T* ust = (const T*)I.ust + 3 * idl;
+        const T* gcl = (const T*)I.gcol + 3 * idl;
+        const T wl = (T)wdl;
         for (int d = 0; d < 3; ++d) {
             u[d] = wl * ust[d];
             gc[d] = wl * gcl[d];
         }
     }
     for (int d = 0; d < 3; ++d) {
-        u[d] = warp_sum(u[d]);
-        gc[d] = warp_sum(gc[d]);
+        u[d] = group8_sum(u[d], gmask);
+        gc[d] = group8_sum(gc[d], gmask);
     }
     const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     T drag[3];
@@ -427,14 +526,12 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     }
     f[2] += fw;
     // ---- reaction of the drag onto the fluid, one stencil node per lane ----
-    if (lane < 8) {
-        if (I.tflag[tile_of(I, id[lane])]) {
-            T* fe = (T*)I.fext + 3 * id[lane];
-            const T c = (T)(-dt * w[lane]);
-            for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
-        } else {
-            err |= ERR_BEAD;
-        }
+    if (I.tflag[tl]) {
+        T* fe = (T*)I.fext + 3 * idl;
+        const T c = (T)(-dt * wdl);
+        for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
+    } else {
+        err |= ERR_BEAD;
     }
     // ---- FP64 integration on lane 0 ----
     if (lane == 0) {
@@ -450,8 +547,8 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
                 I.bvh[3 * a + d] = v2;
                 X[d] = P[d] + dt * v2;
             }
-            X[0] -= I.nx * floor(X[0] / I.nx);
-            X[1] -= I.ny * floor(X[1] / I.ny);
+            X[0] = wrap1(X[0], I.nx);
+            X[1] = wrap1(X[1], I.ny);
             if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) err |= ERR_BEAD;
             for (int d = 0; d < 3; ++d) nxt[3 * a + d] = X[d];
         } else {

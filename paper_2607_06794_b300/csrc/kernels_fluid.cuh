@@ -125,35 +125,36 @@ __device__ __forceinline__ float inv_norm<float>(float g2) { return rsqrtf(g2); 
 template <>
 __device__ __forceinline__ double inv_norm<double>(double g2) { return 1.0 / sqrt(g2); }
 
-// Liquid column height h(x,y) = sum_z (1 + C)/2 of the current moments (Eq. (8)),
-// one thread per column, for instances whose sink is on in this step.
+// Liquid column height h(x,y) = sum_z (1 + C)/2 of the current moments (Eq. (8))
+// for instances whose sink is on in this step.  A block takes 32 columns with 8
+// threads per column, each summing every 8th plane; the 8 partial sums are then
+// added in a fixed order.
+constexpr int HCOL_X = 32, HCOL_Z = 8;
 template <typename T>
-__global__ void k_column_height(const InstDev* __restrict__ insts, const StepGlobals* __restrict__ glob) {
+__global__ void __launch_bounds__(HCOL_X * HCOL_Z) k_column_height(const InstDev* __restrict__ insts,
+                                                                   const StepGlobals* __restrict__ glob) {
     const InstDev& I = insts[blockIdx.y];
     const long long step = __ldcg(&glob->step);
     if (!(I.J0 > 0.0 && I.evap_start >= 0 && step >= I.evap_start) || I.hcol == nullptr) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ T part[HCOL_Z][HCOL_X];
+    const int c = blockIdx.x * HCOL_X + threadIdx.x;
     const unsigned nxy = (unsigned)I.nx * I.ny;
-    if (c >= (int)nxy) return;
+    if (blockIdx.x * HCOL_X >= nxy) return;  // whole block past the last column
     const T* __restrict__ rho = (const T*)I.rho[step % 3];
     const unsigned N = (unsigned)I.N;
     T h = 0;
-    int z = 0;
-    for (; z + 8 <= I.nz; z += 8) {
-        T a[8], b[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            a[k] = rho[(unsigned)(z + k) * nxy + c];
-            b[k] = rho[N + (unsigned)(z + k) * nxy + c];
+    if (c < (int)nxy)
+        for (int z = threadIdx.y; z < I.nz; z += HCOL_Z) {
+            const T a = rho[(unsigned)z * nxy + c], b = rho[N + (unsigned)z * nxy + c];
+            h += (T(1) + qdiv<T>(a - b, a + b)) / T(2);
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) h += (T(1) + (a[k] - b[k]) / (a[k] + b[k])) / T(2);
+    part[threadIdx.y][threadIdx.x] = h;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < (int)nxy) {
+        T s = part[0][threadIdx.x];
+        for (int k = 1; k < HCOL_Z; ++k) s += part[k][threadIdx.x];
+        ((T*)I.hcol)[c] = s;
     }
-    for (; z < I.nz; ++z) {
-        const T a = rho[(unsigned)z * nxy + c], b = rho[N + (unsigned)z * nxy + c];
-        h += (T(1) + (a - b) / (a + b)) / T(2);
-    }
-    ((T*)I.hcol)[c] = h;
 }
 
 template <class S, int TX, int TY>

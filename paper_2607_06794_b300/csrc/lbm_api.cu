@@ -134,6 +134,7 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.tflag = (unsigned*)cv.take(sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int));
             I.tcount = (int*)(I.tflag ? I.tflag + (size_t)I.t8x * I.t8y * I.t8z : nullptr);
             I.tlist = (int*)cv.take(sizeof(int) * (size_t)I.t8x * I.t8y * I.t8z);
+            I.nbit = (unsigned*)cv.take(sizeof(unsigned) * ((size_t)(I.N >> 5) + 1));
             const size_t vb = sizeof(double) * 3 * c.max_beads;
             I.bx = (double*)cv.take(vb);
             I.bv = (double*)cv.take(vb);
@@ -211,6 +212,18 @@ struct lbm_handle {
     bool graph_dirty = true;
     int max_nb = 0;
     int shape = 0;  // index into SHAPES
+    // second stream of a step: column heights and the neighbour list run beside
+    // the coupling-field pass (fork/join by events, captured into the graph)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_begun = nullptr, ev_side = nullptr;
+    ~lbm_handle() {
+        if (side) {
+            cudaStreamSynchronize(side);
+            cudaStreamDestroy(side);
+        }
+        for (cudaEvent_t e : {ev_start, ev_begun, ev_side})
+            if (e) cudaEventDestroy(e);
+    }
 };
 
 #define CK(x)                                   \
@@ -274,33 +287,46 @@ lbm_status set_shape(lbm_handle* h, int k) {
 }
 
 template <class S>
+lbm_status launch_heights(lbm_handle* h, cudaStream_t st);
+
+// The bead phase of a step.  Main stream: clear, step start (with the first
+// kick-drift), coupling fields, then the sub-steps.  Side stream: column
+// heights (from the start of the step) and the neighbour list (after the step
+// start); the sub-steps wait for it.
+template <class S>
 lbm_status launch_beads(lbm_handle* h) {
     using T = typename S::T;
     const int n = (int)h->cfg.size();
-    if (h->max_nb == 0) return LBM_OK;
-    // clear the coupling-tile flags and the cell counts of every instance with beads
-    for (int k = 0; k < n; ++k) {
-        const InstDev& I = h->L.inst[k];
-        if (!I.tflag) continue;
-        CK(cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int), h->stream));
-        CK(cudaMemsetAsync(I.ccount, 0, sizeof(int) * (size_t)I.cgx * I.cgy * I.cgz, h->stream));
-    }
-    const dim3 gw((h->max_nb * 32 + 255) / 256, n);  // one warp per bead
-    const dim3 gt((h->max_nb + 63) / 64, n);         // one thread per bead
-    k_bead_begin<<<gw, 256, 0, h->stream>>>(h->L.d_inst);
+    CK(cudaEventRecord(h->ev_start, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_start, 0));
+    lbm_status st = launch_heights<S>(h, h->side);
+    if (st != LBM_OK) return st;
+    size_t maxclr = 0;
     int maxt = 0;
-    for (auto& I : h->L.inst) maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
+    for (auto& I : h->L.inst) {
+        maxclr = std::max(maxclr, (size_t)I.t8x * I.t8y * I.t8z + 1 + (size_t)I.cgx * I.cgy * I.cgz +
+                                      (size_t)(I.N >> 5) + 1);
+        maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
+    }
+    k_bead_clear<<<dim3((unsigned)std::min<size_t>((maxclr + 255) / 256, 4 * 148), n), 256, 0, h->stream>>>(
+        h->L.d_inst);
+    const dim3 gw((h->max_nb * 32 + 255) / 256, n);  // one warp per bead
+    k_bead_begin<<<gw, 256, 0, h->stream>>>(h->L.d_inst);
+    CK(cudaEventRecord(h->ev_begun, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_begun, 0));
+    k_bead_nlist<<<gw, 256, 0, h->side>>>(h->L.d_inst);
+    CK(cudaEventRecord(h->ev_side, h->side));
     k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
-    k_bead_nlist<<<gw, 256, 0, h->stream>>>(h->L.d_inst);
-    k_bead_kickdrift<<<gt, 64, 0, h->stream>>>(h->L.d_inst);
+    CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));
     const int S_ = h->cfg[0].substeps;
-    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<gw, 256, 0, h->stream>>>(h->L.d_inst, s);
+    const dim3 g8((h->max_nb * BEAD_LANES + 255) / 256, n);  // eight lanes per bead
+    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<g8, 256, 0, h->stream>>>(h->L.d_inst, s);
     CK(cudaGetLastError());
     return LBM_OK;
 }
 
 template <class S>
-lbm_status launch_heights(lbm_handle* h) {
+lbm_status launch_heights(lbm_handle* h, cudaStream_t st) {
     using T = typename S::T;
     int maxc = 0;
     bool any = false;
@@ -309,16 +335,21 @@ lbm_status launch_heights(lbm_handle* h) {
         any |= h->cfg[k].J0 > 0 && h->cfg[k].evap_start >= 0;
     }
     if (!any) return LBM_OK;
-    k_column_height<T><<<dim3((maxc + 255) / 256, (unsigned)h->cfg.size()), 256, 0, h->stream>>>(h->L.d_inst,
-                                                                                             h->L.glob);
+    k_column_height<T><<<dim3((maxc + HCOL_X - 1) / HCOL_X, (unsigned)h->cfg.size()), dim3(HCOL_X, HCOL_Z), 0,
+                         st>>>(h->L.d_inst, h->L.glob);
     CK(cudaGetLastError());
     return LBM_OK;
 }
 
+// everything of a step before the fused fluid kernel (bead phase, column heights)
+template <class S>
+lbm_status launch_prefluid(lbm_handle* h) {
+    return h->max_nb > 0 ? launch_beads<S>(h) : launch_heights<S>(h, h->stream);
+}
+
 template <class S>
 lbm_status enqueue_step(lbm_handle* h) {
-    lbm_status st = launch_beads<S>(h);
-    if (st == LBM_OK) st = launch_heights<S>(h);
+    lbm_status st = launch_prefluid<S>(h);
     if (st != LBM_OK) return st;
     return launch_fused<S>(h);
 }
@@ -673,6 +704,11 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
         delete h;
         return s;
     };
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_begun, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming) != cudaSuccess)
+        return fail(LBM_ECUDA);
     if (cudaMemsetAsync(h->L.glob, 0, sizeof(StepGlobals), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     if (set_shape(h, 0) != LBM_OK) return fail(LBM_ECUDA);
     for (int k = 0; k < n; ++k) {
@@ -859,17 +895,10 @@ lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, doubl
         }
         if (st != LBM_OK) break;
         switch (h->prec) {
-            case LBM_FP64: st = launch_beads<StoreF64>(h); break;
-            case LBM_FP32: st = launch_beads<StoreF32>(h); break;
-            case LBM_FP16_SHIFTED: st = launch_beads<StoreF16>(h); break;
-            default: st = launch_beads<StoreB16>(h); break;
-        }
-        if (st != LBM_OK) break;
-        switch (h->prec) {
-            case LBM_FP64: st = launch_heights<StoreF64>(h); break;
-            case LBM_FP32: st = launch_heights<StoreF32>(h); break;
-            case LBM_FP16_SHIFTED: st = launch_heights<StoreF16>(h); break;
-            default: st = launch_heights<StoreB16>(h); break;
+            case LBM_FP64: st = launch_prefluid<StoreF64>(h); break;
+            case LBM_FP32: st = launch_prefluid<StoreF32>(h); break;
+            case LBM_FP16_SHIFTED: st = launch_prefluid<StoreF16>(h); break;
+            default: st = launch_prefluid<StoreB16>(h); break;
         }
         if (st != LBM_OK) break;
         cudaEventRecord(ev[3 * s + 1], h->stream);

@@ -187,6 +187,7 @@ struct InstDev {
     void* gcol;                  // [N][3] grad C near beads (compute type)
     void* hcol;                  // [ny][nx] liquid column height of the step (compute type)
     unsigned* tflag;             // [t8z][t8y][t8x] coupling-tile flags
+    unsigned* nbit;              // [N/32 + 1] nodes the beads' stencils can reach this step
     int* tlist;                  // flagged tiles of this step (compact)
     int* tcount;                 // number of entries in tlist
     double* cot;                 // [ny][nx] cot(theta)
