@@ -53,6 +53,8 @@ __device__ __forceinline__ double wrap1(double a, int n) { return a < 0.0 ? a + 
 // Positions are kept inside the periodic box by the integrator; a non-finite
 // position (already an error) is mapped to the origin so that no index is
 // ever formed from it.
+// W = double computes the weight in FP64; W = float takes the cell and its
+// fraction in FP64 and the weight in FP32.
 template <typename W>
 __device__ __forceinline__ void stencil_corner(const InstDev& I, const double* X, int c, long long& id, W& w,
                                                int& tile) {
@@ -64,11 +66,11 @@ __device__ __forceinline__ void stencil_corner(const InstDev& I, const double* X
     const int x0 = min(max((int)floor(px), 0), I.nx - 1), y0 = min(max((int)floor(py), 0), I.ny - 1);
     int z0 = (int)floor(pz);
     if (I.nz >= 2 && z0 > I.nz - 2) z0 = I.nz - 2;
-    const double fx = px - x0, fy = py - y0, fz = pz - z0;
+    const W fx = (W)(px - x0), fy = (W)(py - y0), fz = (W)(pz - z0);
     const int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
     const int xx = wrap1(x0 + a, I.nx), yy = wrap1(y0 + b, I.ny), zz = (e && I.nz >= 2) ? z0 + 1 : z0;
     id = ((long long)zz * I.ny + yy) * I.nx + xx;
-    w = (W)((a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy) * (e ? fz : 1.0 - fz));
+    w = (a ? fx : W(1) - fx) * (b ? fy : W(1) - fy) * (e ? fz : W(1) - fz);
     tile = ((zz >> 3) * I.t8y + (yy >> 3)) * I.t8x + (xx >> 3);
 }
 
@@ -125,7 +127,7 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
             I.cbeads[(size_t)c * CELL_CAP + slot] = a;
         else
             atomicOr(I.err, ERR_CAP);
-        const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
+        const double dt = I.dt_sub, hk = I.hk_sub;
         double Y[3];
         for (int d = 0; d < 3; ++d) {
             const double vh = I.bv[3 * a + d] + hk * I.bF[3 * a + d];
@@ -439,11 +441,28 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     const bool last = s == I.substeps;
     const double* cur = (s & 1) ? I.bx2 : I.bx;
     double* nxt = (s & 1) ? I.bx : I.bx2;
-    const double dt = 1.0 / I.substeps, hk = 0.5 * dt / I.mass;
+    const double dt = I.dt_sub, hk = I.hk_sub;
     int err = 0;
     const double P[3] = {cur[3 * a], cur[3 * a + 1], cur[3 * a + 2]};
     const int fa = I.bfil[a], pa = I.bpos[a];
     const int nn = I.nnbr[a];
+    // loads that do not depend on the pair loop go first, so that their latency overlaps it:
+    // this lane's stencil corner with u*, grad C and the tile flag there, the half-step velocity
+    long long idl = 0;
+    T wdl = 0;
+    int tl = 0;
+    stencil_corner(I, P, lane, idl, wdl, tl);
+    T u[3], gc[3];
+    {
+        const T* ust = (const T*)I.ust + 3 * idl;
+        const T* gcl = (const T*)I.gcol + 3 * idl;
+        for (int d = 0; d < 3; ++d) {
+            u[d] = ust[d];
+            gc[d] = gcl[d];
+        }
+    }
+    const unsigned flagged = I.tflag[tl];
+    const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     // ---- pair forces, candidates spread over the lanes ----
     T fx = 0, fy = 0, fz = 0;
     for (int c = lane; c < 4 + nn; c += BEAD_LANES) {
@@ -487,25 +506,13 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     fy = group8_sum(fy, gmask);
     fz = group8_sum(fz, gmask);
     // ---- interpolation of u* and grad C, one stencil node per lane ----
-    long long idl = 0;
-    double wdl = 0.0;
-    int tl = 0;
-    stencil_corner(I, P, lane, idl, wdl, tl);
-    T u[3], gc[3];
     {
-        const T* ust = (const T*)I.ust + 3 * idl;
-        const T* gcl = (const T*)I.gcol + 3 * idl;
         const T wl = (T)wdl;
         for (int d = 0; d < 3; ++d) {
-            u[d] = wl * ust[d];
-            gc[d] = wl * gcl[d];
+            u[d] = group8_sum(wl * u[d], gmask);
+            gc[d] = group8_sum(wl * gc[d], gmask);
         }
     }
-    for (int d = 0; d < 3; ++d) {
-        u[d] = group8_sum(u[d], gmask);
-        gc[d] = group8_sum(gc[d], gmask);
-    }
-    const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     T drag[3];
     for (int d = 0; d < 3; ++d) drag[d] = (T)I.gamma * (u[d] - (T)vh[d]);
     T f[3] = {fx + drag[0] + (T)I.xi * gc[0], fy + drag[1] + (T)I.xi * gc[1], fz + drag[2] + (T)I.xi * gc[2]};
@@ -526,9 +533,9 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
     }
     f[2] += fw;
     // ---- reaction of the drag onto the fluid, one stencil node per lane ----
-    if (I.tflag[tl]) {
+    if (flagged) {
         T* fe = (T*)I.fext + 3 * idl;
-        const T c = (T)(-dt * wdl);
+        const T c = -(T)dt * wdl;
         for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
     } else {
         err |= ERR_BEAD;

@@ -319,8 +319,10 @@ lbm_status launch_beads(lbm_handle* h) {
     k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
     CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));
     const int S_ = h->cfg[0].substeps;
-    const dim3 g8((h->max_nb * BEAD_LANES + 255) / 256, n);  // eight lanes per bead
-    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<g8, 256, 0, h->stream>>>(h->L.d_inst, s);
+    // eight lanes per bead in blocks of 64 threads: the FP64 integration and the
+    // stencil of a few hundred beads spread over as many SMs as possible
+    const dim3 g8((h->max_nb * BEAD_LANES + 63) / 64, n);
+    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<g8, 64, 0, h->stream>>>(h->L.d_inst, s);
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -737,6 +739,8 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
         I.mu = c.mu;
         I.gamma_t = c.gamma_t;
         I.mass = c.bead_mass;
+        I.dt_sub = 1.0 / c.substeps;
+        I.hk_sub = 0.5 * I.dt_sub / c.bead_mass;
         I.rlist = rlist_of(c);
         I.rcon = c.rcon;
         I.x_src = c.x_src;

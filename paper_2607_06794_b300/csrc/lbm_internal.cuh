@@ -209,6 +209,7 @@ struct InstDev {
     int* nbr;
     int* nnbr;
     double ks, Rm, d0, eps_wca, kb, eps_coh, eps_s, rc, gamma, xi, mu, gamma_t, mass, rlist;
+    double dt_sub, hk_sub;       // sub-step 1/substeps and half kick dt/(2 m)
     // cell list of large instances (cells at least rlist wide)
     int cgx, cgy, cgz, pad2;
     int* ccount;                 // beads filed per cell this step
