@@ -104,15 +104,6 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory");
 }
 
-// raw 16-bit element k of a buffer, from the 4-byte word that holds it
-template <class E>
-__device__ __forceinline__ E half_of(unsigned word, unsigned k) {
-    const unsigned short bits = (unsigned short)((k & 1u) ? (word >> 16) : (word & 0xffffu));
-    E e;
-    memcpy(&e, &bits, 2);
-    return e;
-}
-
 template <typename T>
 __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
 template <>
@@ -179,8 +170,8 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     __shared__ double sRed[NT / 32][3];
     __shared__ int sErr;
     // pulled populations of the next plane, staged by asynchronous 4-byte copies
-    // (16- and 32-bit storage; FP64 keeps them in registers): [38][NT] words
-    constexpr bool ASYNC = sizeof(E) == 4;
+    // (16- and 32-bit storage; FP64 keeps them in registers): [19 WORDS][NT] words
+    constexpr bool ASYNC = S::WORDS > 0;
     extern __shared__ __align__(16) unsigned stage_dyn[];
 
     const TileDesc td = tiles[blockIdx.x];
@@ -480,12 +471,11 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
                 const unsigned k = pull_index(z, i);
-                if constexpr (sizeof(E) == 4) {
+                if constexpr (S::WORDS == 2) {
                     cp_async4(st + (size_t)i * NT, src + k);
                     cp_async4(st + (size_t)(19 + i) * NT, src + cs + k);
                 } else {
-                    cp_async4(st + (size_t)i * NT, (const unsigned*)src + (k >> 1));
-                    cp_async4(st + (size_t)(19 + i) * NT, (const unsigned*)src + ((cs + k) >> 1));
+                    cp_async4(st + (size_t)i * NT, (const unsigned*)src + k);
                 }
             });
         }
@@ -547,35 +537,23 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             if constexpr (ASYNC) cp_async_wait<0>();  // plane z landed
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                E eR, eB;
+                // (a bounced-back element has the same weight: w_opp(i) = w_i)
+                T r, b;
                 if constexpr (ASYNC) {
                     const unsigned* st = stage_dyn + tid;
-                    const unsigned wR = st[(size_t)i * NT], wB = st[(size_t)(19 + i) * NT];
-                    if constexpr (sizeof(E) == 4) {
-                        eR = __uint_as_float(wR);
-                        eB = __uint_as_float(wB);
-                    } else {
-                        const unsigned k = pull_index(z, i);
-                        eR = half_of<E>(wR, k);
-                        eB = half_of<E>(wB, cs + k);
-                    }
+                    if constexpr (S::WORDS == 2)
+                        S::decode(__uint_as_float(st[(size_t)i * NT]), __uint_as_float(st[(size_t)(19 + i) * NT]),
+                                  (T)wq(i), rho0, r, b);
+                    else
+                        S::decode_word(st[(size_t)i * NT], (T)wq(i), rho0, r, b);
                 } else {
-                    eR = rawR[i];
-                    eB = rawB[i];
+                    S::decode(rawR[i], rawB[i], (T)wq(i), rho0, r, b);
                 }
-                T r, b;
-                const bool bb = (z - cz(i) < 0) || (z - cz(i) >= nz && top_bc == 0);
                 if (top_gas && cz(i) < 0) {
                     // pure-gas equilibrium streams in; what streamed out is booked
-                    T ro, bo;
-                    S::decode(eR, eB, (T)wq(i), rho0, ro, bo);
-                    (void)ro;
-                    (void)bo;
                     r = T(0);
                     b = (T)wq(i) * rho0;
                     top_in += b;
-                } else {
-                    S::decode(eR, eB, (T)wq(bb ? opp(i) : i), rho0, r, b);
                 }
                 rR += r;
                 rB += b;

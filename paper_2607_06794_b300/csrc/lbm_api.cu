@@ -114,8 +114,7 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
         I.top_bc = c.top_bc;
         I.N = (long long)c.nx * c.ny * c.nz;
         const size_t eb = elem_bytes(c.prec), cb = comp_bytes(c.prec);
-        // +16 bytes: 16-bit storage is staged in 4-byte words that may reach 2 bytes past
-        for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb + 16);
+        for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb);
         for (int p = 0; p < 3; ++p) I.rho[p] = cv.take(2 * I.N * cb);
         I.cot = (double*)cv.take(sizeof(double) * c.nx * c.ny);
         I.hcol = cv.take(cb * c.nx * c.ny);
@@ -239,7 +238,7 @@ namespace {
 // dynamic shared memory of the fused kernel: the staged pull of one plane
 template <class S>
 constexpr size_t stage_bytes(int nt) {
-    return sizeof(typename S::E) == 4 ? (size_t)38 * nt * 4 : 0;
+    return (size_t)19 * S::WORDS * nt * 4;
 }
 
 template <class S, int TX, int TY>

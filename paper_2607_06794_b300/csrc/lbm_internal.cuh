@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 namespace lbm {
 
 // ---------------------------------------------------------------------------
@@ -40,14 +42,19 @@ __host__ __device__ constexpr double inv_len(int i) {
 enum : int { ERR_NAN = 1, ERR_FENE = 2, ERR_BEAD = 4, ERR_TIMEOUT = 8, ERR_CAP = 16 };
 
 // ---------------------------------------------------------------------------
-// Population storage.  Layout per buffer: [comp][dir][z][y][x], comp stride
-// 19*N, dir stride N.  load() returns (f^R, f^B) in the compute type; store()
-// writes a post-collision pair and returns the values as they will be read
-// back (quantised), so moments pushed from them match the next pull exactly.
+// Population storage.  Element k = i N + node of direction i.  FP64 and FP32
+// lay a buffer out as [comp][dir][z][y][x] (comp stride cs = 19 N); the 16-bit
+// forms keep both numbers of an element in one 4-byte word, [dir][z][y][x].
+// WORDS = 4-byte words per element and component layout (2: two planes of
+// 4-byte values, 1: one word per element; 0: not staged in words).  load()
+// returns (f^R, f^B) in the compute type; store() writes a post-collision pair
+// and returns the values as they will be read back (quantised), so moments
+// pushed from them match the next pull exactly.
 // ---------------------------------------------------------------------------
 struct StoreF64 {
     using T = double;
     using E = double;
+    static constexpr int WORDS = 0;
     static __device__ __forceinline__ void decode(E a, E c, T w, T rho0, T& r, T& b) {
         r = a;
         b = c;
@@ -79,6 +86,7 @@ struct StoreF64 {
 struct StoreF32 {
     using T = float;
     using E = float;
+    static constexpr int WORDS = 2;
     static __device__ __forceinline__ void decode(E a, E c, T w, T rho0, T& r, T& b) {
         r = a;
         b = c;
@@ -131,42 +139,45 @@ template <class H>
 struct StoreShift16 {
     using T = float;
     using E = H;
+    static constexpr int WORDS = 1;
     static __host__ __device__ __forceinline__ void decode(float P, float psi, float w, float rho0,
                                                            float& r, float& b) {
         float F = P + w * rho0;
         r = (psi + 0.5f) * F;
         b = F - r;
     }
-    static __device__ __forceinline__ void decode(H P, H psi, float w, float rho0, float& r, float& b) {
-        decode(Cvt<H>::f(P), Cvt<H>::f(psi), w, rho0, r, b);
+    // one element as its 4-byte word: low half P, high half psi
+    static __device__ __forceinline__ void decode_word(unsigned word, float w, float rho0, float& r,
+                                                       float& b) {
+        H h[2];
+        memcpy(h, &word, 4);
+        decode(Cvt<H>::f(h[0]), Cvt<H>::f(h[1]), w, rho0, r, b);
     }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
-        float P = Cvt<H>::f(p[k]);
-        float psi = Cvt<H>::f(p[cs + k]);
-        decode(P, psi, w, rho0, r, b);
+        decode_word(__ldg((const unsigned*)p + k), w, rho0, r, b);
     }
     static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         float F = r + b;
-        H qP = Cvt<H>::h(F - w * rho0);
-        H qs = Cvt<H>::h(F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f);
-        p[k] = qP;
-        p[cs + k] = qs;
-        decode(Cvt<H>::f(qP), Cvt<H>::f(qs), w, rho0, rq, bq);
+        H h[2] = {Cvt<H>::h(F - w * rho0), Cvt<H>::h(F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f)};
+        unsigned word;
+        memcpy(&word, h, 4);
+        ((unsigned*)p)[k] = word;
+        decode(Cvt<H>::f(h[0]), Cvt<H>::f(h[1]), w, rho0, rq, bq);
     }
     static __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                   double& r, double& b) {
         float rr, bb;
-        decode(Cvt<H>::f(p[k]), Cvt<H>::f(p[cs + k]), (float)wq(i), (float)rho0, rr, bb);
+        decode(Cvt<H>::f(p[2 * k]), Cvt<H>::f(p[2 * k + 1]), (float)wq(i), (float)rho0, rr, bb);
         r = rr;
         b = bb;
     }
     static __device__ void from_f64(E* p, long long cs, long long k, int i, double rho0, double r,
                                     double b) {
         float F = (float)(r + b);
-        p[k] = Cvt<H>::h(F - (float)wq(i) * (float)rho0);
-        p[cs + k] = Cvt<H>::h(F != 0.0f ? (float)(r / (r + b)) - 0.5f : 0.0f);
+        p[2 * k] = Cvt<H>::h(F - (float)wq(i) * (float)rho0);
+        p[2 * k + 1] = Cvt<H>::h(F != 0.0f ? (float)(r / (r + b)) - 0.5f : 0.0f);
     }
 };
 using StoreF16 = StoreShift16<__half>;
