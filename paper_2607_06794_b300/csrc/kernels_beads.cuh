@@ -146,15 +146,31 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
     int z = fz + dz;
     z = z < 0 ? 0 : (z >= I.nz ? I.nz - 1 : z);
     const int t = ((z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3);
-    // most tiles are already flagged by a neighbour: read before the atomic
-    if (!((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u) I.tlist[atomicAdd(I.tcount, 1)] = t;
-    // the 4x4x4 nodes the stencil can reach during the step, two per lane
+    // one lane per distinct tile of the warp; most tiles are already flagged by a
+    // neighbour, so the flag is read before the atomic; new tiles are appended
+    // with one counter update per warp
+    const unsigned same_t = __match_any_sync(0xffffffffu, t);
+    bool fresh = false;
+    if (lane == __ffs(same_t) - 1)
+        fresh = !((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u;
+    const unsigned fresh_m = __ballot_sync(0xffffffffu, fresh);
+    if (fresh_m) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(I.tcount, __popc(fresh_m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) I.tlist[base + __popc(fresh_m & ((1u << lane) - 1u))] = t;
+    }
+    // the 4x4x4 nodes the stencil can reach during the step, two per lane; the bits of
+    // one 32-node word are gathered in the warp and set by one lane
     for (int k = 0; k < 2; ++k) {
         const int zr = fz + (lane >> 4) * 2 + k - 1;
         const int zz = zr < 0 ? 0 : (zr >= I.nz ? I.nz - 1 : zr);
         const long long node = ((long long)zz * I.ny + y) * I.nx + x;
-        const unsigned bit = 1u << (node & 31);
-        if (!(((volatile unsigned*)I.nbit)[node >> 5] & bit)) atomicOr(I.nbit + (node >> 5), bit);
+        const unsigned word = (unsigned)(node >> 5);
+        const unsigned same_w = __match_any_sync(0xffffffffu, word);
+        const unsigned bits = __reduce_or_sync(same_w, 1u << (node & 31));
+        if (lane == __ffs(same_w) - 1 && (((volatile unsigned*)I.nbit)[word] & bits) != bits)
+            atomicOr(I.nbit + word, bits);
     }
 }
 

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     const int x = x0 + tx, y = y0 + ty;
 
     const T rho0 = (T)Ig.rho0, itR = T(1) / (T)Ig.tau_R, itB = T(1) / (T)Ig.tau_B;
+    const unsigned step_key = hash32((unsigned)step * 0x9e3779b9u + (unsigned)td.inst);
     const T beta = (T)Ig.beta;
     const T hsig = T(0.5) * (T)Ig.sigma;
     const T bfx = (T)Ig.body[0], bfy = (T)Ig.body[1], bfz = (T)Ig.body[2];
@@ -631,7 +632,10 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     evap_sum += d;
                 }
                 T rq, bq;
-                S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
+                if constexpr (i == 0)  // the sink's population: stochastic rounding in 16-bit storage
+                    S::store_sr(dst, cs, node, w, rho0, r, b, rq, bq, hash32(node ^ step_key));
+                else
+                    S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
                 const int tz = z + cz(i);  // the same for the whole block
                 if (tz < 0 || (tz >= nz && top_bc == 0)) {
                     ac0[1][0] += rq;  // bounces back to this node

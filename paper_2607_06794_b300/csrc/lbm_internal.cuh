@@ -51,6 +51,17 @@ enum : int { ERR_NAN = 1, ERR_FENE = 2, ERR_BEAD = 4, ERR_TIMEOUT = 8, ERR_CAP =
 // and returns the values as they will be read back (quantised), so moments
 // pushed from them match the next pull exactly.
 // ---------------------------------------------------------------------------
+// 32-bit integer hash (Wellons' "lowbias32"): the counter-based uniform source
+// of the stochastic rounding below
+__host__ __device__ __forceinline__ unsigned hash32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 struct StoreF64 {
     using T = double;
     using E = double;
@@ -70,6 +81,10 @@ struct StoreF64 {
         p[cs + k] = b;
         rq = r;
         bq = b;
+    }
+    static __device__ __forceinline__ void store_sr(E* __restrict__ p, unsigned cs, unsigned k, T w,
+                                                    T rho0, T r, T b, T& rq, T& bq, unsigned) {
+        store(p, cs, k, w, rho0, r, b, rq, bq);
     }
     static __host__ __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                            double& r, double& b) {
@@ -103,6 +118,10 @@ struct StoreF32 {
         rq = r;
         bq = b;
     }
+    static __device__ __forceinline__ void store_sr(E* __restrict__ p, unsigned cs, unsigned k, T w,
+                                                    T rho0, T r, T b, T& rq, T& bq, unsigned) {
+        store(p, cs, k, w, rho0, r, b, rq, bq);
+    }
     static __host__ __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                            double& r, double& b) {
         r = p[k];
@@ -124,6 +143,8 @@ template <>
 struct Cvt<__half> {
     static __device__ __forceinline__ float f(__half h) { return __half2float(h); }
     static __device__ __forceinline__ __half h(float f) { return __float2half_rn(f); }
+    static __device__ __forceinline__ __half rd(float f) { return __float2half_rd(f); }
+    static __device__ __forceinline__ __half ru(float f) { return __float2half_ru(f); }
     static __host__ __device__ float fh(__half h) { return __half2float(h); }
     static __host__ __device__ __half hf(float f) { return __float2half_rn(f); }
 };
@@ -131,6 +152,8 @@ template <>
 struct Cvt<__nv_bfloat16> {
     static __device__ __forceinline__ float f(__nv_bfloat16 h) { return __bfloat162float(h); }
     static __device__ __forceinline__ __nv_bfloat16 h(float f) { return __float2bfloat16_rn(f); }
+    static __device__ __forceinline__ __nv_bfloat16 rd(float f) { return __float2bfloat16_rd(f); }
+    static __device__ __forceinline__ __nv_bfloat16 ru(float f) { return __float2bfloat16_ru(f); }
     static __host__ __device__ float fh(__nv_bfloat16 h) { return __bfloat162float(h); }
     static __host__ __device__ __nv_bfloat16 hf(float f) { return __float2bfloat16_rn(f); }
 };
@@ -161,6 +184,22 @@ struct StoreShift16 {
                                                  T rho0, T r, T b, T& rq, T& bq) {
         float F = r + b;
         H h[2] = {Cvt<H>::h(F - w * rho0), Cvt<H>::h(F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f)};
+        unsigned word;
+        memcpy(&word, h, 4);
+        ((unsigned*)p)[k] = word;
+        decode(Cvt<H>::f(h[0]), Cvt<H>::f(h[1]), w, rho0, rq, bq);
+    }
+    // the same with the liquid fraction rounded stochastically (up with probability
+    // (x - lo)/(hi - lo), rnd a uniform 32-bit number): per-step changes far below one
+    // unit of the last place, such as the evaporation sink's, survive on average
+    static __device__ __forceinline__ void store_sr(E* __restrict__ p, unsigned cs, unsigned k, T w,
+                                                    T rho0, T r, T b, T& rq, T& bq, unsigned rnd) {
+        float F = r + b;
+        const float x = F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f;
+        const H lo = Cvt<H>::rd(x), hi = Cvt<H>::ru(x);
+        const float flo = Cvt<H>::f(lo), fhi = Cvt<H>::f(hi);
+        const float u = (float)(rnd >> 8) * (1.0f / 16777216.0f);
+        H h[2] = {Cvt<H>::h(F - w * rho0), (u * (fhi - flo) < x - flo) ? hi : lo};
         unsigned word;
         memcpy(&word, h, 4);
         ((unsigned*)p)[k] = word;
