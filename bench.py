@@ -29,17 +29,23 @@ METRIC = "2-comp D3Q19 MLUPS & % HBM roofline; FP16-store+batched vs FP32 plain"
 # in FP64).
 ALG_BYTES = {"fp64": 640, "fp32": 320, "fp16": 168, "bf16": 168}
 
-# DRAM bytes per launch of the fused kernel from one ncu capture, keyed by the
-# hash of the kernel sources when they were taken (null once sources change).
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the fused kernel from one ncu capture
+# (profiles/k_stream_collide_c2_fp32.md), keyed by the hash of the kernel source
+# when they were taken and the workload; null once the source changes.
+TRAFFIC = {("3d0a4b3917ae", "c2_256x128x64_stripe_200wires"): 361139456 + 306495488}
 
 
 def kernel_hash():
-    """Hash of the sources of the fused kernel (its file and the shared storage policies)."""
-    h = hashlib.sha1()
+    """Hash of the fused kernel's source: the k_stream_collide template and the shared
+    storage policies it compiles against."""
     d = os.path.join(ROOT, "paper_2607_06794_b300", "csrc")
-    for f in ("kernels_fluid.cuh", "lbm_internal.cuh"):
-        h.update(open(os.path.join(d, f), "rb").read())
+    src = open(os.path.join(d, "kernels_fluid.cuh")).read()
+    i = src.index("k_stream_collide(const InstDev")
+    start = src.rindex("template <class S, int TX, int TY>", 0, i)
+    end = src.index("\n}\n", i) + 3
+    h = hashlib.sha1()
+    h.update(src[start:end].encode())
+    h.update(open(os.path.join(d, "lbm_internal.cuh"), "rb").read())
     return h.hexdigest()[:12]
 
 
