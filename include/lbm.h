@@ -239,6 +239,21 @@ lbm_status lbm_deposit_profiles(lbm_handle* h, int inst, int axis, double lo, do
                                 double centre, double half_width, double* S_x, double* g,
                                 int* n_bonds, int* n_beads);
 
+/* Droplet-shape observables of instance `inst` at its current step, the
+ * quantities tracked for the pure droplet on a patch (Sec. III.A, Fig. 2):
+ * liquid column height h(x,y) = sum_z (1 + C)/2; volume = sum h; height = max h;
+ * centre = h-weighted centroid; footprint radii r_x, r_y = half the positive
+ * runs of C on the first fluid layer (z = 0) through the centre along x and y,
+ * ends at the linearly interpolated C = 0 crossings; contact angles
+ * theta = 2 atan(height / r) in degrees (spherical-cap relation in each
+ * principal section); v_x (v_y) = mean of j_x/rho (j_y/rho) over the liquid
+ * nodes (C > 0) of the column at (x_c + r_x/2, y_c) ((x_c, y_c + r_y/2)).
+ * Synchronises the stream. */
+typedef struct {
+    double volume, height, xc, yc, r_x, r_y, theta_x, theta_y, v_x, v_y;
+} lbm_shape;
+lbm_status lbm_droplet_shape(lbm_handle* h, int inst, lbm_shape* out);
+
 /* Release the handle (the workspace stays the caller's). */
 lbm_status lbm_destroy(lbm_handle* h);
 

@@ -239,6 +239,12 @@ class Simulation:
                "lbm_deposit_profiles")
         return S, g, nb, nd
 
+    def shape(self, inst) -> dict:
+        """Droplet height, volume, centre, footprint radii, contact angles and mean flow."""
+        d = _lib.lbm_shape()
+        _check(self.L.lbm_droplet_shape(self.h, inst, C.byref(d)), "lbm_droplet_shape")
+        return {k: getattr(d, k) for k, _ in _lib.lbm_shape._fields_}
+
     def close(self):
         if getattr(self, "h", None):
             self.L.lbm_destroy(self.h)

@@ -19,7 +19,8 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_substrate_pattern", "lb
            "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
            "lbm_deposit_descriptors", "lbm_destroy", "lbm_status_string", "lbm_mlp_param_count",
            "lbm_mlp_scratch_bytes", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
-           "lbm_deposit_descriptors_noalloc", "lbm_deposit_conductivity", "lbm_deposit_profiles")
+           "lbm_deposit_descriptors_noalloc", "lbm_deposit_conductivity", "lbm_deposit_profiles",
+           "lbm_droplet_shape")
 
 
 class lbm_config(C.Structure):
@@ -54,6 +55,11 @@ class lbm_conductivity(C.Structure):
         ("residual", C.c_double), ("iterations", C.c_int), ("n_src", C.c_int), ("n_snk", C.c_int),
         ("n_edges", C.c_int),
     ]
+
+
+class lbm_shape(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("volume", "height", "xc", "yc", "r_x", "r_y", "theta_x",
+                                          "theta_y", "v_x", "v_y")]
 
 
 _lib = None
@@ -114,6 +120,8 @@ def load():
     L.lbm_deposit_profiles.restype = C.c_int
     L.lbm_deposit_profiles.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
                                        C.c_double, dp, dp, ip, ip]
+    L.lbm_droplet_shape.restype = C.c_int
+    L.lbm_droplet_shape.argtypes = [vp, C.c_int, C.POINTER(lbm_shape)]
     L.lbm_status_string.restype = C.c_char_p
     L.lbm_status_string.argtypes = [C.c_int]
     _lib = L

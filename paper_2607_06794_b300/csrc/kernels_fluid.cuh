@@ -238,6 +238,14 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     };
 
     const T hcol = (evap_on && active) ? hcolm[y * nx + x] : T(0);
+    // coupling-tile flags of this thread's column for the 8-plane slabs of the chunk,
+    // read once (bit s: slab (z0 >> 3) + s), so that no plane waits on a flag load
+    unsigned tbits = 0u;
+    if (tflag != nullptr && active) {
+        const int s0 = z0 >> 3, s1 = min((z1 - 1) >> 3, s0 + 31);
+        for (int sl = s0; sl <= s1; ++sl)
+            if (tflag[(sl * t8y + (y >> 3)) * t8x + (x >> 3)]) tbits |= 1u << (sl - s0);
+    }
 
     for (int s = tid; s < 3 * 2 * HY1 * TX; s += NT) (&sB[0][0][0][0])[s] = T(0);
     if (tid == 0) sErr = 0;
@@ -587,7 +595,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             const V4 G = sG[z & 1][ty][tx];
             const T Gx = G.x, Gy = G.y, Gz = G.z;
             T Fx = hsig * kap * Gx + bfx, Fy = hsig * kap * Gy + bfy, Fz = hsig * kap * Gz + bfz;
-            if (tflag != nullptr && tflag[((z >> 3) * t8y + (y >> 3)) * t8x + (x >> 3)]) {
+            if ((tbits >> ((z >> 3) - (z0 >> 3))) & 1u) {
                 const T* fe = fext + 3 * (size_t)node;
                 Fx += fe[0];
                 Fy += fe[1];
@@ -755,6 +763,46 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
 // and after populations are written from the host.  Writes rho[pr] (both
 // components) and clears the next buffer.
 // ---------------------------------------------------------------------------
+// rho_R, rho_B, j of node n from the populations that stream into it at `step`
+template <class S>
+__device__ void stream_moments(const InstDev& I, long long step, long long n, typename S::T* m) {
+    using T = typename S::T;
+    using E = typename S::E;
+    const long long N = I.N;
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    const E* src = (const E*)I.pop[step & 1];
+    const long long cs = 19 * N;
+    const T rho0 = (T)I.rho0;
+    T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sz = z - cz(i);
+        T r, b;
+        if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
+            S::load(src, cs, (long long)opp(i) * N + n, (T)wq(opp(i)), rho0, r, b);
+        } else if (sz >= nz) {
+            r = T(0);
+            b = (T)wq(i) * rho0;
+        } else {
+            const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
+            S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i),
+                    rho0, r, b);
+        }
+        rR += r;
+        rB += b;
+        const T F = r + b;
+        jx += cx(i) * F;
+        jy += cy(i) * F;
+        jz += cz(i) * F;
+    }
+    m[0] = rR;
+    m[1] = rB;
+    m[2] = jx;
+    m[3] = jy;
+    m[4] = jz;
+}
+
 template <class S>
 __global__ void k_moments(InstDev I, long long step, long long n0, long long len,
                           double* __restrict__ diag) {

@@ -16,6 +16,7 @@
 #include "../../include/lbm.h"
 #include "kernels_beads.cuh"
 #include "kernels_network.cuh"
+#include "kernels_shape.cuh"
 
 using namespace lbm;
 
@@ -68,11 +69,14 @@ double rlist_of(const lbm_config& c) {
     return rl + 1.0;
 }
 
+// planes per block: at most 240 (241 with a merged last plane) so that a chunk spans at most 32 coupling-tile
+// slabs of 8 planes (the fused kernel keeps their flags in one 32-bit mask)
+constexpr int MAX_CHUNK = 240;
 int chunk_z(const lbm_config& c, const Shape& sh) {
-    if (sh.chunk > 0) return std::max(2, std::min(sh.chunk, c.nz));
+    if (sh.chunk > 0) return std::max(2, std::min(std::min(sh.chunk, MAX_CHUNK), c.nz));
     // enough blocks to fill the GPU on small lattices
     const long long cols = (long long)((c.nx + sh.tx - 1) / sh.tx) * ((c.ny + sh.ty - 1) / sh.ty);
-    int ch = c.nz;
+    int ch = std::min(c.nz, MAX_CHUNK);
     while (cols * ((c.nz + ch - 1) / ch) < 4 * 148 && ch > 8) ch = (ch + 1) / 2;
     return std::max(2, std::min(ch, c.nz));
 }
@@ -659,6 +663,24 @@ lbm_status place_random(lbm_handle* h, int k, int nw, int nbf, double spacing, u
     return got == nw ? LBM_OK : LBM_EINVAL;
 }
 
+template <class S>
+lbm_status droplet_shape(lbm_handle* h, int inst, double* res) {
+    using T = typename S::T;
+    const InstDev& I = h->L.inst[inst];
+    const size_t ncol = (size_t)I.nx * I.ny;
+    if ((ncol + 16) * sizeof(double) > h->L.stage_bytes) return LBM_ENOMEM_WS;
+    double* out = h->L.stage;  // [4] sums, then h(x,y)
+    double* dres = out + 4;
+    double* hbuf = out + 16;
+    CK(cudaMemsetAsync(out, 0, 16 * sizeof(double), h->stream));
+    k_shape_columns<T><<<(unsigned)((ncol + 255) / 256), 256, 0, h->stream>>>(I, h->step, hbuf, out);
+    k_shape_finish<S><<<1, 32, 0, h->stream>>>(I, h->step, out, dres);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(res, dres, 10 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1192,6 +1214,31 @@ lbm_status lbm_deposit_profiles(lbm_handle* h, int inst, int axis, double lo, do
     if (n_bonds) CK(cudaMemcpyAsync(n_bonds, bd, sizeof(int) * nbins, cudaMemcpyDeviceToHost, h->stream));
     if (n_beads) CK(cudaMemcpyAsync(n_beads, nd, sizeof(int) * nbins, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return latched(h);
+}
+
+lbm_status lbm_droplet_shape(lbm_handle* h, int inst, lbm_shape* out) {
+    if (!valid_inst(h, inst) || !out) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    double r[10];
+    lbm_status st;
+    switch (h->prec) {
+        case LBM_FP64: st = droplet_shape<StoreF64>(h, inst, r); break;
+        case LBM_FP32: st = droplet_shape<StoreF32>(h, inst, r); break;
+        case LBM_FP16_SHIFTED: st = droplet_shape<StoreF16>(h, inst, r); break;
+        default: st = droplet_shape<StoreB16>(h, inst, r); break;
+    }
+    if (st != LBM_OK) return st;
+    out->volume = r[0];
+    out->height = r[1];
+    out->xc = r[2];
+    out->yc = r[3];
+    out->r_x = r[4];
+    out->r_y = r[5];
+    out->theta_x = r[6];
+    out->theta_y = r[7];
+    out->v_x = r[8];
+    out->v_y = r[9];
     return latched(h);
 }
 
