@@ -623,14 +623,17 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             }
             const T rGx = Gx * ig, rGy = Gy * ig, rGz = Gz * ig;
             const T base0 = T(1) - T(1.5) * usq;
-            auto emit = [&](auto I_, T post) {
+            const T omc = T(1) - omega;
+            // recolouring weight beta (rho_R rho_B / rho) w_i / |c_i| of the two direction classes
+            const T cw_axis = coef * T(1.0 / 18.0), cw_diag = coef * T(1.0 / 36.0 / 1.4142135623730951);
+            // post = the colour-blind post-collision population of direction i;
+            // cG = c_i . G / |G| (sign included)
+            auto emit = [&](auto I_, T post, T cG) {
                 constexpr int i = decltype(I_)::value;
                 constexpr T w = (T)wq(i);
-                T cG = 0;
-                if constexpr (cx(i) != 0) cG += cx(i) * rGx;
-                if constexpr (cy(i) != 0) cG += cy(i) * rGy;
-                if constexpr (cz(i) != 0) cG += cz(i) * rGz;
-                T r = phi * post + coef * w * (cG * (T)inv_len(i));
+                constexpr bool axis = (cx(i) != 0) + (cy(i) != 0) + (cz(i) != 0) == 1;
+                T r = phi * post;
+                if constexpr (i != 0) r += (axis ? cw_axis : cw_diag) * cG;
                 T b = post - r;
                 if (i == 0 && evap_on) {
                     T d = dm > r ? r : dm;
@@ -681,28 +684,28 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                     }
                 }
             };
+            // BGK with the Guo source, post_i = (1 - omega) F_i + omega F_i^eq + S_i, written per
+            // direction pair (i, opp(i)): F^eq = even +- odd, S = se +- so with
+            //   even = w rho (1 - 1.5 u.u + 4.5 (c.u)^2), odd = 3 w rho c.u,
+            //   se = (1 - omega/2) w (9 (c.u)(c.F) - 3 u.F), so = 3 (1 - omega/2) w c.F
             {  // rest direction
                 constexpr T w = (T)wq(0);
-                const T feq = w * rho * base0;
-                const T Sg = gsrc * w * (T(-3) * uF);
-                emit(std::integral_constant<int, 0>{}, Fi[0] - omega * (Fi[0] - feq) + Sg);
+                const T pre = omega * (w * rho * base0) + gsrc * w * (T(-3) * uF);
+                emit(std::integral_constant<int, 0>{}, omc * Fi[0] + pre, T(0));
             }
             static_for<1, 19, 2>([&](auto I_) {
                 // the pair (i, opp(i) = i+1) shares c.u, c.F and c.G up to sign
                 constexpr int i = decltype(I_)::value;
                 constexpr T w = (T)wq(i);
-                T cu = 0, cF = 0;
-                if constexpr (cx(i) != 0) { cu += cx(i) * ux; cF += cx(i) * Fx; }
-                if constexpr (cy(i) != 0) { cu += cy(i) * uy; cF += cy(i) * Fy; }
-                if constexpr (cz(i) != 0) { cu += cz(i) * uz; cF += cz(i) * Fz; }
-                const T wr = w * rho;
-                const T even = wr * (base0 + T(4.5) * cu * cu);
-                const T odd = wr * (T(3) * cu);
-                const T se = gsrc * w * (T(9) * cu * cF - T(3) * uF);
-                const T so = gsrc * w * (T(3) * cF);
-                emit(std::integral_constant<int, i>{}, Fi[i] - omega * (Fi[i] - (even + odd)) + (se + so));
-                emit(std::integral_constant<int, i + 1>{},
-                     Fi[i + 1] - omega * (Fi[i + 1] - (even - odd)) + (se - so));
+                T cu = 0, cF = 0, cG = 0;
+                if constexpr (cx(i) != 0) { cu += cx(i) * ux; cF += cx(i) * Fx; cG += cx(i) * rGx; }
+                if constexpr (cy(i) != 0) { cu += cy(i) * uy; cF += cy(i) * Fy; cG += cy(i) * rGy; }
+                if constexpr (cz(i) != 0) { cu += cz(i) * uz; cF += cz(i) * Fz; cG += cz(i) * rGz; }
+                const T ow = omega * (w * rho), gw = gsrc * w;
+                const T A = ow * (base0 + T(4.5) * cu * cu) + gw * (T(9) * cu * cF - T(3) * uF);
+                const T B = ow * (T(3) * cu) + gw * (T(3) * cF);
+                emit(std::integral_constant<int, i>{}, omc * Fi[i] + (A + B), cG);
+                emit(std::integral_constant<int, i + 1>{}, omc * Fi[i + 1] + (A - B), -cG);
             });
             if (top_gas) {
                 // gas inflow that the next stream brings to this node

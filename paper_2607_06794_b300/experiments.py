@@ -42,3 +42,27 @@ def e1_drying(steps=20000, every=500, prec="fp32", theta_r=30.0, J0=None):
     out["rx_tilde"] = out["r_x"] / h0
     out["ry_tilde"] = out["r_y"] / h0
     return out
+
+
+def main(argv=None):
+    """python -m paper_2607_06794_b300.experiments [--steps N] [--every K] [--J0 J] [--theta_r T]:
+    prints one JSON line per record of the E1 drying run."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--every", type=int, default=500)
+    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--theta_r", type=float, default=30.0)
+    ap.add_argument("--J0", type=float, default=None)
+    a = ap.parse_args(argv)
+    r = e1_drying(a.steps, a.every, a.prec, a.theta_r, a.J0)
+    for k in range(len(r["step"])):
+        print(json.dumps({key: (int(r[key][k]) if key == "step" else round(float(r[key][k]), 6))
+                          for key in ("step", "volume", "h_tilde", "rx_tilde", "ry_tilde", "theta_x",
+                                      "theta_y", "v_x", "v_y")}))
+
+
+if __name__ == "__main__":
+    main()
