@@ -83,20 +83,30 @@ __device__ __forceinline__ int cell_of(const InstDev& I, float x, float y, float
     return (cz_ * I.cgy + cy_) * I.cgx + cx_;
 }
 
-// Clear the coupling-tile flags (and the flagged-tile count behind them) and
-// the cell counts of every instance with beads, before the step's bead phase.
-__global__ void k_bead_clear(const InstDev* __restrict__ insts) {
+// Flag set of the step a bead start prepares: the current step (ahead = 0), or
+// the step after the one whose sub-steps just ran (ahead = 1: the sub-step pass
+// recorded it, so the answer does not depend on whether the fused kernel,
+// which advances the step counter, has finished)
+__device__ __forceinline__ int start_parity(const StepGlobals* glob, int ahead) {
+    return (int)((ahead ? __ldcg(&glob->bead_next) : __ldcg(&glob->step)) & 1);
+}
+
+// Clear the coupling-tile flags (and the flagged-tile count behind them), the
+// reach bits and the cell counts of every instance with beads, before its bead start.
+__global__ void k_bead_clear(const InstDev* __restrict__ insts, const StepGlobals* __restrict__ glob, int ahead) {
     const InstDev& I = insts[blockIdx.y];
     if (I.tflag == nullptr) return;
-    const int nt = I.t8x * I.t8y * I.t8z + 1, nc = I.cgx * I.cgy * I.cgz;
-    const int nw = (int)(I.N >> 5) + 1;
+    const int p = start_parity(glob, ahead);
+    unsigned* tflag = tflag_of(I, p);
+    unsigned* nbit = nbit_of(I, p);
+    const int nt = I.ntile + 1, nc = I.cgx * I.cgy * I.cgz, nw = I.nword;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt + nc + nw; i += gridDim.x * blockDim.x) {
         if (i < nt)
-            I.tflag[i] = 0u;
+            tflag[i] = 0u;
         else if (i < nt + nc)
             I.ccount[i - nt] = 0;
         else
-            I.nbit[i - nt - nc] = 0u;
+            nbit[i - nt - nc] = 0u;
     }
 }
 
@@ -105,7 +115,7 @@ __global__ void k_bead_clear(const InstDev* __restrict__ insts) {
 // kick and drift of the step (FP64, lane 0), and flag the coupling tiles its
 // trilinear stencil can reach during the step (lane = one corner of the 4x4x2
 // reach; duplicates are harmless).
-__global__ void k_bead_begin(const InstDev* __restrict__ insts) {
+__global__ void k_bead_begin(const InstDev* __restrict__ insts, const StepGlobals* __restrict__ glob, int ahead) {
     const InstDev I = insts[blockIdx.y];
     const int lane = threadIdx.x & 31;
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -149,16 +159,19 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
     // one lane per distinct tile of the warp; most tiles are already flagged by a
     // neighbour, so the flag is read before the atomic; new tiles are appended
     // with one counter update per warp
+    const int p = start_parity(glob, ahead);
+    unsigned* tflag = tflag_of(I, p);
+    unsigned* nbit = nbit_of(I, p);
     const unsigned same_t = __match_any_sync(0xffffffffu, t);
     bool fresh = false;
     if (lane == __ffs(same_t) - 1)
-        fresh = !((volatile unsigned*)I.tflag)[t] && atomicExch(I.tflag + t, 1u) == 0u;
+        fresh = !((volatile unsigned*)tflag)[t] && atomicExch(tflag + t, 1u) == 0u;
     const unsigned fresh_m = __ballot_sync(0xffffffffu, fresh);
     if (fresh_m) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(I.tcount, __popc(fresh_m));
+        if (lane == 0) base = atomicAdd(tcount_of(I, p), __popc(fresh_m));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (fresh) I.tlist[base + __popc(fresh_m & ((1u << lane) - 1u))] = t;
+        if (fresh) tlist_of(I, p)[base + __popc(fresh_m & ((1u << lane) - 1u))] = t;
     }
     // the 4x4x4 nodes the stencil can reach during the step, two per lane; the bits of
     // one 32-node word are gathered in the warp and set by one lane
@@ -169,8 +182,8 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts) {
         const unsigned word = (unsigned)(node >> 5);
         const unsigned same_w = __match_any_sync(0xffffffffu, word);
         const unsigned bits = __reduce_or_sync(same_w, 1u << (node & 31));
-        if (lane == __ffs(same_w) - 1 && (((volatile unsigned*)I.nbit)[word] & bits) != bits)
-            atomicOr(I.nbit + word, bits);
+        if (lane == __ffs(same_w) - 1 && (((volatile unsigned*)nbit)[word] & bits) != bits)
+            atomicOr(nbit + word, bits);
     }
 }
 
@@ -185,9 +198,10 @@ __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ 
     using E = typename S::E;
     const InstDev* Ip = insts + blockIdx.y;
     if (Ip->tflag == nullptr || Ip->nb == 0) return;
-    const int ntl = *Ip->tcount;
+    const int p = (int)(__ldcg(&glob->step) & 1);
+    const int ntl = *tcount_of(*Ip, p);
     for (int it = blockIdx.x; it < ntl; it += gridDim.x) {
-        bead_field_tile<S>(Ip, glob, Ip->tlist[it]);
+        bead_field_tile<S>(Ip, glob, tlist_of(*Ip, p)[it]);
         __syncthreads();
     }
 }
@@ -294,7 +308,7 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     T* fe = (T*)I.fext + 3 * node;
     fe[0] = fe[1] = fe[2] = T(0);
     // u* and grad C are read only inside the beads' reach (marked at the step start)
-    if (!((I.nbit[node >> 5] >> (node & 31)) & 1u)) return;
+    if (!((nbit_of(I, (int)(step & 1))[node >> 5] >> (node & 31)) & 1u)) return;
     T gx = 0, gy = 0, gz = 0, kap = 0;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -448,8 +462,10 @@ __device__ __forceinline__ T group8_sum(T v, unsigned mask) {
 // FP64 (second half kick; if not last, the next first half kick and drift).
 constexpr int BEAD_LANES = 8;
 template <typename T>
-__global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
+__global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __restrict__ glob, int s) {
     const InstDev I = insts[blockIdx.y];
+    const long long step = __ldcg(&glob->step);
+    if (s == I.substeps && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) glob->bead_next = step + 1;
     const int lane = threadIdx.x & (BEAD_LANES - 1);
     const unsigned gmask = 0xffu << (threadIdx.x & 24);
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) / BEAD_LANES;
@@ -477,7 +493,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, int s) {
             gc[d] = gcl[d];
         }
     }
-    const unsigned flagged = I.tflag[tl];
+    const unsigned flagged = tflag_of(I, (int)(step & 1))[tl];
     const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     // ---- pair forces, candidates spread over the lanes ----
     T fx = 0, fy = 0, fz = 0;

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     T* __restrict__ rho_w = (T*)Ig.rho[(pr + 1) % 3];
     T* __restrict__ rho_z = (T*)Ig.rho[(pr + 2) % 3];
     const T* __restrict__ fext = (const T*)Ig.fext;
-    const unsigned* __restrict__ tflag = Ig.tflag;
+    const unsigned* __restrict__ tflag = Ig.tflag ? tflag_of(Ig, (int)(step & 1)) : nullptr;
     const double* __restrict__ cotm = Ig.cot;
     const T* __restrict__ hcolm = (const T*)Ig.hcol;
     double* accp = Ig.acc;
@@ -926,12 +926,12 @@ __global__ void k_colour(InstDev I, long long step, long long n0, long long len,
 
 // Bead force on the fluid, FP64 copy of a node range
 template <typename T>
-__global__ void k_fext(InstDev I, long long n0, long long len, double* __restrict__ out) {
+__global__ void k_fext(InstDev I, int parity, long long n0, long long len, double* __restrict__ out) {
     const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (u >= 3 * len || I.fext == nullptr) return;
     const long long n = n0 + u / 3;
     const int x = (int)(n % I.nx), y = (int)((n / I.nx) % I.ny), z = (int)(n / ((long long)I.nx * I.ny));
-    const bool live = I.tflag[((long long)(z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3)] != 0;
+    const bool live = tflag_of(I, parity)[((long long)(z >> 3) * I.t8y + (y >> 3)) * I.t8x + (x >> 3)] != 0;
     out[u] = live ? (double)((const T*)I.fext)[3 * n0 + u] : 0.0;
 }
 

@@ -134,10 +134,11 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.fext = cv.take(3 * I.N * cb);
             I.ust = cv.take(3 * I.N * cb);
             I.gcol = cv.take(3 * I.N * cb);
-            I.tflag = (unsigned*)cv.take(sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int));
-            I.tcount = (int*)(I.tflag ? I.tflag + (size_t)I.t8x * I.t8y * I.t8z : nullptr);
-            I.tlist = (int*)cv.take(sizeof(int) * (size_t)I.t8x * I.t8y * I.t8z);
-            I.nbit = (unsigned*)cv.take(sizeof(unsigned) * ((size_t)(I.N >> 5) + 1));
+            I.ntile = I.t8x * I.t8y * I.t8z;
+            I.nword = (int)(I.N >> 5) + 1;
+            I.tflag = (unsigned*)cv.take(sizeof(unsigned) * 2 * ((size_t)I.ntile + 1));
+            I.tlist = (int*)cv.take(sizeof(int) * 2 * (size_t)I.ntile);
+            I.nbit = (unsigned*)cv.take(sizeof(unsigned) * 2 * (size_t)I.nword);
             const size_t vb = sizeof(double) * 3 * c.max_beads;
             I.bx = (double*)cv.take(vb);
             I.bv = (double*)cv.take(vb);
@@ -218,13 +219,16 @@ struct lbm_handle {
     // second stream of a step: column heights and the neighbour list run beside
     // the coupling-field pass (fork/join by events, captured into the graph)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_begun = nullptr, ev_side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_begun = nullptr, ev_side = nullptr, ev_forced = nullptr, ev_next = nullptr;
+    // the bead start (flags, cells, neighbour list, first kick-drift) of the current
+    // step has been enqueued; every step then enqueues the start of the next one
+    bool beads_ready = false;
     ~lbm_handle() {
         if (side) {
             cudaStreamSynchronize(side);
             cudaStreamDestroy(side);
         }
-        for (cudaEvent_t e : {ev_start, ev_begun, ev_side})
+        for (cudaEvent_t e : {ev_start, ev_begun, ev_side, ev_forced, ev_next})
             if (e) cudaEventDestroy(e);
     }
 };
@@ -292,41 +296,58 @@ lbm_status set_shape(lbm_handle* h, int k) {
 template <class S>
 lbm_status launch_heights(lbm_handle* h, cudaStream_t st);
 
-// The bead phase of a step.  Main stream: clear, step start (with the first
-// kick-drift), coupling fields, then the sub-steps.  Side stream: column
-// heights (from the start of the step) and the neighbour list (after the step
-// start); the sub-steps wait for it.
+// Bead start of a step on stream st: clear the flag set, step-start kernel
+// (cells, flags, reach bits, first kick-drift), neighbour list.  ahead = 1 starts
+// the step after the one whose sub-steps have run (it overlaps that step's fused
+// kernel); ahead = 0 starts the current step (the first one, or after the host
+// changed the beads).
+lbm_status launch_bead_start(lbm_handle* h, cudaStream_t st, int ahead) {
+    const int n = (int)h->cfg.size();
+    size_t maxclr = 0;
+    for (auto& I : h->L.inst)
+        maxclr = std::max(maxclr, (size_t)I.ntile + 1 + (size_t)I.cgx * I.cgy * I.cgz + (size_t)I.nword);
+    k_bead_clear<<<dim3((unsigned)std::min<size_t>((maxclr + 255) / 256, 4 * 148), n), 256, 0, st>>>(
+        h->L.d_inst, h->L.glob, ahead);
+    const dim3 gw((h->max_nb * 32 + 255) / 256, n);  // one warp per bead
+    k_bead_begin<<<gw, 256, 0, st>>>(h->L.d_inst, h->L.glob, ahead);
+    k_bead_nlist<<<gw, 256, 0, st>>>(h->L.d_inst);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+// One step with beads.  Main stream: coupling fields, the sub-steps, the fused
+// kernel.  Side stream: column heights (from the start of the step), then, once
+// the sub-steps are done, the start of the next step beside the fused kernel;
+// the step ends when both streams have.  Events, if given, bracket the fused launch.
 template <class S>
-lbm_status launch_beads(lbm_handle* h) {
+lbm_status launch_bead_step(lbm_handle* h, cudaEvent_t before, cudaEvent_t after) {
     using T = typename S::T;
     const int n = (int)h->cfg.size();
     CK(cudaEventRecord(h->ev_start, h->stream));
     CK(cudaStreamWaitEvent(h->side, h->ev_start, 0));
     lbm_status st = launch_heights<S>(h, h->side);
     if (st != LBM_OK) return st;
-    size_t maxclr = 0;
-    int maxt = 0;
-    for (auto& I : h->L.inst) {
-        maxclr = std::max(maxclr, (size_t)I.t8x * I.t8y * I.t8z + 1 + (size_t)I.cgx * I.cgy * I.cgz +
-                                      (size_t)(I.N >> 5) + 1);
-        maxt = std::max(maxt, I.t8x * I.t8y * I.t8z);
-    }
-    k_bead_clear<<<dim3((unsigned)std::min<size_t>((maxclr + 255) / 256, 4 * 148), n), 256, 0, h->stream>>>(
-        h->L.d_inst);
-    const dim3 gw((h->max_nb * 32 + 255) / 256, n);  // one warp per bead
-    k_bead_begin<<<gw, 256, 0, h->stream>>>(h->L.d_inst);
-    CK(cudaEventRecord(h->ev_begun, h->stream));
-    CK(cudaStreamWaitEvent(h->side, h->ev_begun, 0));
-    k_bead_nlist<<<gw, 256, 0, h->side>>>(h->L.d_inst);
     CK(cudaEventRecord(h->ev_side, h->side));
+    int maxt = 0;
+    for (auto& I : h->L.inst) maxt = std::max(maxt, I.ntile);
     k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
-    CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));
     const int S_ = h->cfg[0].substeps;
     // eight lanes per bead in blocks of 64 threads: the FP64 integration and the
     // stencil of a few hundred beads spread over as many SMs as possible
     const dim3 g8((h->max_nb * BEAD_LANES + 63) / 64, n);
-    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<g8, 64, 0, h->stream>>>(h->L.d_inst, s);
+    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<g8, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
     CK(cudaGetLastError());
+    CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));  // column heights before the fused kernel
+    CK(cudaEventRecord(h->ev_forced, h->stream));
+    CK(cudaStreamWaitEvent(h->side, h->ev_forced, 0));
+    st = launch_bead_start(h, h->side, 1);
+    if (st != LBM_OK) return st;
+    CK(cudaEventRecord(h->ev_next, h->side));
+    if (before) CK(cudaEventRecord(before, h->stream));
+    st = launch_fused<S>(h);
+    if (st != LBM_OK) return st;
+    if (after) CK(cudaEventRecord(after, h->stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_next, 0));
     return LBM_OK;
 }
 
@@ -346,17 +367,26 @@ lbm_status launch_heights(lbm_handle* h, cudaStream_t st) {
     return LBM_OK;
 }
 
-// everything of a step before the fused fluid kernel (bead phase, column heights)
+// one step: with beads the pipelined bead step; else column heights, fused kernel
+// (events, if given, bracket the fused launch on the handle's stream)
 template <class S>
-lbm_status launch_prefluid(lbm_handle* h) {
-    return h->max_nb > 0 ? launch_beads<S>(h) : launch_heights<S>(h, h->stream);
+lbm_status enqueue_step(lbm_handle* h, cudaEvent_t before = nullptr, cudaEvent_t after = nullptr) {
+    if (h->max_nb > 0) return launch_bead_step<S>(h, before, after);
+    lbm_status st = launch_heights<S>(h, h->stream);
+    if (st != LBM_OK) return st;
+    if (before) CK(cudaEventRecord(before, h->stream));
+    st = launch_fused<S>(h);
+    if (st != LBM_OK) return st;
+    if (after) CK(cudaEventRecord(after, h->stream));
+    return LBM_OK;
 }
 
-template <class S>
-lbm_status enqueue_step(lbm_handle* h) {
-    lbm_status st = launch_prefluid<S>(h);
-    if (st != LBM_OK) return st;
-    return launch_fused<S>(h);
+// the bead start of the current step, once after creation or a host change of the beads
+lbm_status ensure_bead_start(lbm_handle* h) {
+    if (h->max_nb == 0 || h->beads_ready) return LBM_OK;
+    lbm_status st = launch_bead_start(h, h->stream, 0);
+    if (st == LBM_OK) h->beads_ready = true;
+    return st;
 }
 
 lbm_status enqueue_step_any(lbm_handle* h) {
@@ -475,7 +505,8 @@ lbm_status node_field(lbm_handle* h, int k, unsigned field, double* host) {
         else if (field == LBM_FIELD_COLOUR)
             k_colour<T><<<nb, bt, 0, h->stream>>>(I, h->step, n0, len, h->L.stage);
         else
-            k_fext<T><<<nb, bt, 0, h->stream>>>(I, n0, len, h->L.stage);
+            // the flag set of the last fused launch (step - 1)
+            k_fext<T><<<nb, bt, 0, h->stream>>>(I, (int)((h->step + 1) & 1), n0, len, h->L.stage);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(host + per * n0, h->L.stage, per * len * sizeof(double), cudaMemcpyDeviceToHost,
                            h->stream));
@@ -730,7 +761,9 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
     if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_begun, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&h->ev_side, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_forced, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_next, cudaEventDisableTiming) != cudaSuccess)
         return fail(LBM_ECUDA);
     if (cudaMemsetAsync(h->L.glob, 0, sizeof(StepGlobals), h->stream) != cudaSuccess) return fail(LBM_ECUDA);
     if (set_shape(h, 0) != LBM_OK) return fail(LBM_ECUDA);
@@ -778,8 +811,7 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
             if (cudaMemsetAsync(I.fext, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
                 cudaMemsetAsync(I.ust, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
                 cudaMemsetAsync(I.gcol, 0, 3 * I.N * cb, h->stream) != cudaSuccess ||
-                cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * (size_t)I.t8x * I.t8y * I.t8z + sizeof(int),
-                                h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.tflag, 0, sizeof(unsigned) * 2 * ((size_t)I.ntile + 1), h->stream) != cudaSuccess ||
                 cudaMemsetAsync(I.bF, 0, sizeof(double) * 3 * c.max_beads, h->stream) != cudaSuccess)
                 return fail(LBM_ECUDA);
         }
@@ -871,12 +903,17 @@ lbm_status lbm_add_nanowires(lbm_handle* h, int inst, int n_wires, double length
     I.nb += nadd;
     h->max_nb = 0;
     for (auto& J : h->L.inst) h->max_nb = std::max(h->max_nb, J.nb);
+    h->beads_ready = false;
     return upload_tables(h);
 }
 
 lbm_status lbm_step(lbm_handle* h, int n_steps) {
     if (!h || n_steps < 0) return LBM_EINVAL;
     const int n = (int)h->cfg.size();
+    if (n_steps > 0) {
+        lbm_status st = ensure_bead_start(h);
+        if (st != LBM_OK) return st;
+    }
     for (int s = 0; s < n_steps; ++s) {
         // h0 is taken from the moments of the first evaporating step
         for (int k = 0; k < n; ++k) {
@@ -911,7 +948,7 @@ lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, doubl
                 if (f) cudaEventDestroy(f);
             return LBM_ECUDA;
         }
-    lbm_status st = LBM_OK;
+    lbm_status st = ensure_bead_start(h);
     for (int s = 0; s < n_steps && st == LBM_OK; ++s) {
         cudaEventRecord(ev[3 * s], h->stream);
         for (int k = 0; k < n && st == LBM_OK; ++k) {
@@ -920,20 +957,11 @@ lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, doubl
         }
         if (st != LBM_OK) break;
         switch (h->prec) {
-            case LBM_FP64: st = launch_prefluid<StoreF64>(h); break;
-            case LBM_FP32: st = launch_prefluid<StoreF32>(h); break;
-            case LBM_FP16_SHIFTED: st = launch_prefluid<StoreF16>(h); break;
-            default: st = launch_prefluid<StoreB16>(h); break;
+            case LBM_FP64: st = enqueue_step<StoreF64>(h, ev[3 * s + 1], ev[3 * s + 2]); break;
+            case LBM_FP32: st = enqueue_step<StoreF32>(h, ev[3 * s + 1], ev[3 * s + 2]); break;
+            case LBM_FP16_SHIFTED: st = enqueue_step<StoreF16>(h, ev[3 * s + 1], ev[3 * s + 2]); break;
+            default: st = enqueue_step<StoreB16>(h, ev[3 * s + 1], ev[3 * s + 2]); break;
         }
-        if (st != LBM_OK) break;
-        cudaEventRecord(ev[3 * s + 1], h->stream);
-        switch (h->prec) {
-            case LBM_FP64: st = launch_fused<StoreF64>(h); break;
-            case LBM_FP32: st = launch_fused<StoreF32>(h); break;
-            case LBM_FP16_SHIFTED: st = launch_fused<StoreF16>(h); break;
-            default: st = launch_fused<StoreB16>(h); break;
-        }
-        cudaEventRecord(ev[3 * s + 2], h->stream);
         ++h->step;
     }
     cudaEventRecord(ev[3 * (size_t)n_steps], h->stream);
@@ -1104,6 +1132,7 @@ lbm_status lbm_write_fields(lbm_handle* h, int inst, unsigned field, const void*
             if (I.nb == 0) return LBM_OK;
             double* p = field == LBM_FIELD_BEAD_X ? I.bx : (field == LBM_FIELD_BEAD_V ? I.bv : I.bF);
             CK(cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice));
+            h->beads_ready = false;  // the next step starts the beads again
             return LBM_OK;
         }
         case LBM_FIELD_ACCUM: {
@@ -1111,8 +1140,9 @@ lbm_status lbm_write_fields(lbm_handle* h, int inst, unsigned field, const void*
             if (a[0] < 0 || a[0] != floor(a[0])) return LBM_EINVAL;
             // the step counter is shared by all instances of the handle
             h->step = (long long)a[0];
-            StepGlobals g{h->step, 0u, 0};
+            StepGlobals g{h->step, 0u, 0, h->step};
             CK(cudaMemcpy(h->L.glob, &g, sizeof(g), cudaMemcpyHostToDevice));
+            h->beads_ready = false;  // the flag set follows the step's parity
             double v[8] = {a[0], a[1], a[2], a[3], a[4], 0, 0, 0};
             CK(cudaMemcpy(I.acc, v, sizeof(v), cudaMemcpyHostToDevice));
             return LBM_OK;

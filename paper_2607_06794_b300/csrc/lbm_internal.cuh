@@ -236,10 +236,12 @@ struct InstDev {
     void* ust;                   // [N][3] u* near beads (compute type)
     void* gcol;                  // [N][3] grad C near beads (compute type)
     void* hcol;                  // [ny][nx] liquid column height of the step (compute type)
-    unsigned* tflag;             // [t8z][t8y][t8x] coupling-tile flags
-    unsigned* nbit;              // [N/32 + 1] nodes the beads' stencils can reach this step
-    int* tlist;                  // flagged tiles of this step (compact)
-    int* tcount;                 // number of entries in tlist
+    // per-step coupling flags in two sets by step parity: the next step's set is
+    // filled while the fused kernel still reads this step's
+    unsigned* tflag;             // [2][ntile + 1]: [t8z][t8y][t8x] tile flags, then the flagged-tile count
+    int* tlist;                  // [2][ntile]: flagged tiles (compact)
+    unsigned* nbit;              // [2][nword]: nodes the beads' stencils can reach in the step
+    int ntile, nword;            // t8z t8y t8x and N/32 + 1
     double* cot;                 // [ny][nx] cot(theta)
     double* acc;                 // [8]: step, h0, evaporated, top_in, top_out, ...
     int* err;                    // latched error bits
@@ -286,7 +288,15 @@ struct StepGlobals {
     long long step;
     unsigned int done;
     int pad;
+    long long bead_next;  // step whose bead start the last sub-step pass enabled (step + 1)
 };
+
+__device__ __forceinline__ unsigned* tflag_of(const InstDev& I, int p) {
+    return I.tflag + (size_t)p * (I.ntile + 1);
+}
+__device__ __forceinline__ int* tcount_of(const InstDev& I, int p) { return (int*)(tflag_of(I, p) + I.ntile); }
+__device__ __forceinline__ int* tlist_of(const InstDev& I, int p) { return I.tlist + (size_t)p * I.ntile; }
+__device__ __forceinline__ unsigned* nbit_of(const InstDev& I, int p) { return I.nbit + (size_t)p * I.nword; }
 
 struct TileDesc {
     int inst, x0, y0, z0, z1, pad0, pad1, pad2;
