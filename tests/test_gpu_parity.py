@@ -330,3 +330,31 @@ def test_large_bead_instance_uses_cell_list_and_matches_oracle(lbm, oracle):
     assert np.allclose(sim.read(0, "bead_x"), ob.X, atol=1e-11)
     assert np.allclose(sim.read(0, "bead_f"), ob.F, atol=1e-11)
     assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-11
+
+
+def test_checkpoint_restore_with_beads_continues_the_run(lbm, oracle):
+    """Fields read from a run and written into a fresh handle (step counter first, then the
+    populations and the bead state) continue exactly as the original run does."""
+    cfg = droplet_cfg(lbm, nx=48, ny=32, nz=20, prec="fp64", max_beads=40, xi=0.02, a=18, b=11, c=14,
+                      J0=1e-3, evap_start=0)
+    p, fR, fB, cot = oracle_state(oracle, cfg, 3)
+    fil, pos, X = bead_case(cfg, seed=31, n_fil=4)
+    cen = X.reshape(4, 4, 3).mean(axis=1)
+    dirs = X.reshape(4, 4, 3)[:, -1] - X.reshape(4, 4, 3)[:, 0]
+    a = lbm.Simulation([cfg])
+    a.write(0, "populations", np.stack([fR, fB]))
+    a.add_nanowires(0, 4, 8.0, cen, dirs)
+    a.step(3)
+    saved = {f: a.read(0, f) for f in ("accum", "populations", "bead_x", "bead_v", "bead_f")}
+    b = lbm.Simulation([cfg])
+    b.write(0, "accum", saved["accum"])
+    b.write(0, "populations", saved["populations"])
+    b.add_nanowires(0, 4, 8.0, cen, dirs)
+    for f in ("bead_x", "bead_v", "bead_f"):
+        b.write(0, f, saved[f])
+    a.step(3)
+    b.step(3)
+    assert b.status() == 0 and a.status() == 0
+    assert np.allclose(b.read(0, "bead_x"), a.read(0, "bead_x"), rtol=0, atol=1e-12)
+    pa, pb = a.read(0, "populations"), b.read(0, "populations")
+    assert np.max(np.abs(pa - pb)) < 1e-12
