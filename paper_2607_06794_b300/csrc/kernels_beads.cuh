@@ -447,28 +447,29 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// sum over the 8 lanes of one bead's group (mask: the group's lanes)
-template <typename T>
-__device__ __forceinline__ T group8_sum(T v, unsigned mask) {
-    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+// sum over the L lanes of one bead's group (mask: the group's lanes)
+template <int L, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
 
-// Force evaluation of sub-step s (1-based), eight lanes per bead (four beads
-// per warp): the lanes share the bonded partners and the neighbour list (pair
-// forces in the compute type) and take one stencil node each for the
-// interpolation of u* and grad C and for the reaction spread; the group's
+// Force evaluation of sub-step s (1-based), L lanes per bead (8 or 16): the
+// lanes share the bonded partners and the neighbour list (pair forces in the
+// compute type); lanes 0..7 take one stencil node each for the interpolation
+// of u* and grad C and for the reaction spread; the group's
 // first lane adds drag, solvation, adhesion and friction and integrates in
 // FP64 (second half kick; if not last, the next first half kick and drift).
-constexpr int BEAD_LANES = 8;
-template <typename T>
+template <typename T, int L>
 __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __restrict__ glob, int s) {
+    static_assert(L >= 8 && L <= 32 && (L & (L - 1)) == 0, "8, 16 or 32 lanes per bead");
     const InstDev I = insts[blockIdx.y];
     const long long step = __ldcg(&glob->step);
     if (s == I.substeps && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) glob->bead_next = step + 1;
-    const int lane = threadIdx.x & (BEAD_LANES - 1);
-    const unsigned gmask = 0xffu << (threadIdx.x & 24);
-    const int a = (blockIdx.x * blockDim.x + threadIdx.x) / BEAD_LANES;
+    const int lane = threadIdx.x & (L - 1);
+    const bool corner = lane < 8;  // lanes 0..7 take the eight trilinear corners
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (threadIdx.x & (32 - L)));
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) / L;
     if (a >= I.nb) return;  // a whole group leaves together
     const bool last = s == I.substeps;
     const double* cur = (s & 1) ? I.bx2 : I.bx;
@@ -483,21 +484,22 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     long long idl = 0;
     T wdl = 0;
     int tl = 0;
-    stencil_corner(I, P, lane, idl, wdl, tl);
-    T u[3], gc[3];
-    {
+    T u[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
+    unsigned flagged = 1u;
+    if (corner) {
+        stencil_corner(I, P, lane, idl, wdl, tl);
         const T* ust = (const T*)I.ust + 3 * idl;
         const T* gcl = (const T*)I.gcol + 3 * idl;
         for (int d = 0; d < 3; ++d) {
             u[d] = ust[d];
             gc[d] = gcl[d];
         }
+        flagged = tflag_of(I, (int)(step & 1))[tl];
     }
-    const unsigned flagged = tflag_of(I, (int)(step & 1))[tl];
     const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     // ---- pair forces, candidates spread over the lanes ----
     T fx = 0, fy = 0, fz = 0;
-    for (int c = lane; c < 4 + nn; c += BEAD_LANES) {
+    for (int c = lane; c < 4 + nn; c += L) {
         int b;
         bool same;
         int sep;
@@ -534,15 +536,15 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
             fz += gr * d2;
         }
     }
-    fx = group8_sum(fx, gmask);
-    fy = group8_sum(fy, gmask);
-    fz = group8_sum(fz, gmask);
+    fx = group_sum<L>(fx, gmask);
+    fy = group_sum<L>(fy, gmask);
+    fz = group_sum<L>(fz, gmask);
     // ---- interpolation of u* and grad C, one stencil node per lane ----
     {
         const T wl = (T)wdl;
         for (int d = 0; d < 3; ++d) {
-            u[d] = group8_sum(wl * u[d], gmask);
-            gc[d] = group8_sum(wl * gc[d], gmask);
+            u[d] = group_sum<L>(wl * u[d], gmask);
+            gc[d] = group_sum<L>(wl * gc[d], gmask);
         }
     }
     T drag[3];
@@ -565,12 +567,14 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     }
     f[2] += fw;
     // ---- reaction of the drag onto the fluid, one stencil node per lane ----
-    if (flagged) {
-        T* fe = (T*)I.fext + 3 * idl;
-        const T c = -(T)dt * wdl;
-        for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
-    } else {
-        err |= ERR_BEAD;
+    if (corner) {
+        if (flagged) {
+            T* fe = (T*)I.fext + 3 * idl;
+            const T c = -(T)dt * wdl;
+            for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
+        } else {
+            err |= ERR_BEAD;
+        }
     }
     // ---- FP64 integration on lane 0 ----
     if (lane == 0) {

@@ -25,6 +25,28 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
+// deterministic block sums of two values per thread
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+        red[w] = a;
+        red[32 + w] = b;
+    }
+    __syncthreads();
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        sa += red[k];
+        sb += red[32 + k];
+    }
+    a = sa;
+    b = sb;
+}
+
 // conductance and end points of edge e (bond or contact) with its nearest-image length
 __device__ __forceinline__ double edge_conductance(const InstDev& I, int a, int b) {
     const double dx = min_image(I.bx[3 * b] - I.bx[3 * a], I.nx),
@@ -42,24 +64,27 @@ __device__ __forceinline__ double edge_conductance(const InstDev& I, int a, int 
 //      leaving the source and entering the sink, kappa* (Eq. (18)).
 // Output I.netout: kappa, I_tot, I_sink, I_ref, residual, iterations, n_src,
 // n_snk, n_edges, converged.
+// dynamic shared memory: the search direction p when the instance's beads fit (p_smem)
 __global__ void __launch_bounds__(NET_THREADS) k_net_solve(const InstDev* __restrict__ insts, int only,
-                                                           double tol, int max_iter) {
+                                                           double tol, int max_iter, int p_smem) {
     const InstDev I = insts[only];
     const int n = I.nb, nbm = I.nb_max;
     const int ne = min(*I.nedges, I.max_edges);
     const int tid = threadIdx.x, NTH = blockDim.x;
     double* V = I.net;
     double* r = V + nbm;
-    double* p = r + nbm;
-    double* q = p + nbm;
+    extern __shared__ double p_sh[];
+    double* q = r + 2 * (size_t)nbm;
     double* dinv = q + nbm;
     double* cur = dinv + nbm;
+    double* p = p_smem ? p_sh : r + nbm;  // zero on the fixed nodes throughout
+    double* diag = cur;                   // sum_j G_ij during the solve; the node currents after it
     int* row = I.csr_row;   // [nbm + 1]
     int* cnt = I.csr_cnt;   // [nbm]
     int* cls = cnt + nbm;   // [nbm]: 1 source, 2 sink, 0 free
     int* col = I.csr_col;   // [2 max_edges]
     double* val = I.csr_val;
-    __shared__ double red[32];
+    __shared__ double red[64];
     __shared__ int scan[NET_THREADS];
 
     for (int a = tid; a < n; a += NTH) {
@@ -130,6 +155,7 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_solve(const InstDev* __rest
         }
         const bool fr = cls[a] == 0;
         V[a] = cls[a] == 1 ? 1.0 : 0.0;
+        diag[a] = d;
         dinv[a] = (fr && d > 0.0) ? 1.0 / d : 0.0;
         r[a] = fr ? b : 0.0;  // start from V = 0 on the free nodes
         p[a] = dinv[a] * r[a];
@@ -143,16 +169,15 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_solve(const InstDev* __rest
     const double stop = tol * tol * bb;
     while (it < max_iter && rr > stop && rz > 0.0) {
         // q = A p on the free rows: A_ii = sum_j G_ij, A_ij = -G_ij (j free)
+        // (p vanishes on the fixed nodes, so their columns drop out by themselves)
         double pq = 0.0;
         for (int a = tid; a < n; a += NTH) {
             double v = 0.0;
             if (cls[a] == 0) {
-                double off = 0.0, d = 0.0;
-                for (int s = row[a]; s < row[a + 1]; ++s) {
-                    d += val[s];
-                    if (cls[col[s]] == 0) off += val[s] * p[col[s]];
-                }
-                v = d * p[a] - off;
+                double off = 0.0;
+                const int s1 = row[a + 1];
+                for (int s = row[a]; s < s1; ++s) off += val[s] * p[col[s]];
+                v = diag[a] * p[a] - off;
             }
             q[a] = v;
             pq += p[a] * v;
@@ -169,8 +194,7 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_solve(const InstDev* __rest
             rz1 += r[a] * dinv[a] * r[a];
             rr1 += r[a] * r[a];
         }
-        rz1 = block_sum(rz1, red);
-        rr1 = block_sum(rr1, red);
+        block_sum2(rz1, rr1, red);
         const double beta = rz1 / rz;
         rz = rz1;
         rr = rr1;

@@ -332,10 +332,19 @@ lbm_status launch_bead_step(lbm_handle* h, cudaEvent_t before, cudaEvent_t after
     for (auto& I : h->L.inst) maxt = std::max(maxt, I.ntile);
     k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
     const int S_ = h->cfg[0].substeps;
-    // eight lanes per bead in blocks of 64 threads: the FP64 integration and the
-    // stencil of a few hundred beads spread over as many SMs as possible
-    const dim3 g8((h->max_nb * BEAD_LANES + 63) / 64, n);
-    for (int s = 1; s <= S_; ++s) k_bead_force<T><<<g8, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
+    // blocks of 64 threads, so that the FP64 integration and the stencils of a few
+    // hundred beads spread over many SMs; sixteen lanes per bead up to 2048 beads in
+    // the whole batch (measured faster at 800), eight beyond (more beads per warp:
+    // faster at 16,000 in one lattice and at 18,000 over 64)
+    int total_nb = 0;
+    for (auto& I : h->L.inst) total_nb += I.nb;
+    if (total_nb <= 2048) {
+        const dim3 g((h->max_nb * 16 + 63) / 64, n);
+        for (int s = 1; s <= S_; ++s) k_bead_force<T, 16><<<g, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
+    } else {
+        const dim3 g((h->max_nb * 8 + 63) / 64, n);
+        for (int s = 1; s <= S_; ++s) k_bead_force<T, 8><<<g, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));  // column heights before the fused kernel
     CK(cudaEventRecord(h->ev_forced, h->stream));
@@ -1197,7 +1206,12 @@ lbm_status lbm_deposit_conductivity(lbm_handle* h, int inst, double tol, int max
     if (I.nb_max == 0) return latched(h);
     CK(cudaMemsetAsync(I.nedges, 0, sizeof(int), h->stream));
     if (I.nb > 0) k_desc_edges<<<(I.nb + 127) / 128, 128, 0, h->stream>>>(h->L.d_inst, inst);
-    k_net_solve<<<1, NET_THREADS, 0, h->stream>>>(h->L.d_inst, inst, tol, max_iter);
+    // the search direction in shared memory when it fits (up to 25,600 beads)
+    const size_t p_bytes = sizeof(double) * (size_t)I.nb_max;
+    const int p_smem = p_bytes <= (size_t)200 * 1024 ? 1 : 0;
+    if (p_smem)
+        CK(cudaFuncSetAttribute(k_net_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_bytes));
+    k_net_solve<<<1, NET_THREADS, p_smem ? p_bytes : 0, h->stream>>>(h->L.d_inst, inst, tol, max_iter, p_smem);
     CK(cudaGetLastError());
     double o[10];
     CK(cudaMemcpyAsync(o, I.netout, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
