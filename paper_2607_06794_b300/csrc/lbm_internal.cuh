@@ -147,6 +147,18 @@ struct Cvt<__half> {
     static __device__ __forceinline__ __half ru(float f) { return __float2half_ru(f); }
     static __host__ __device__ float fh(__half h) { return __half2float(h); }
     static __host__ __device__ __half hf(float f) { return __float2half_rn(f); }
+    // a pair in one word (lo in the low half) and back, with the packed conversions
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        const __half2 v = __floats2half2_rn(lo, hi);
+        unsigned w;
+        memcpy(&w, &v, 4);
+        return w;
+    }
+    static __device__ __forceinline__ float2 unpack(unsigned w) {
+        __half2 v;
+        memcpy(&v, &w, 4);
+        return __half22float2(v);
+    }
 };
 template <>
 struct Cvt<__nv_bfloat16> {
@@ -156,6 +168,17 @@ struct Cvt<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 ru(float f) { return __float2bfloat16_ru(f); }
     static __host__ __device__ float fh(__nv_bfloat16 h) { return __bfloat162float(h); }
     static __host__ __device__ __nv_bfloat16 hf(float f) { return __float2bfloat16_rn(f); }
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        unsigned w;
+        memcpy(&w, &v, 4);
+        return w;
+    }
+    static __device__ __forceinline__ float2 unpack(unsigned w) {
+        __nv_bfloat162 v;
+        memcpy(&v, &w, 4);
+        return __bfloat1622float2(v);
+    }
 };
 
 template <class H>
@@ -172,9 +195,8 @@ struct StoreShift16 {
     // one element as its 4-byte word: low half P, high half psi
     static __device__ __forceinline__ void decode_word(unsigned word, float w, float rho0, float& r,
                                                        float& b) {
-        H h[2];
-        memcpy(h, &word, 4);
-        decode(Cvt<H>::f(h[0]), Cvt<H>::f(h[1]), w, rho0, r, b);
+        const float2 v = Cvt<H>::unpack(word);
+        decode(v.x, v.y, w, rho0, r, b);
     }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
@@ -183,11 +205,9 @@ struct StoreShift16 {
     static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         float F = r + b;
-        H h[2] = {Cvt<H>::h(F - w * rho0), Cvt<H>::h(F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f)};
-        unsigned word;
-        memcpy(&word, h, 4);
+        const unsigned word = Cvt<H>::pack(F - w * rho0, F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f);
         ((unsigned*)p)[k] = word;
-        decode(Cvt<H>::f(h[0]), Cvt<H>::f(h[1]), w, rho0, rq, bq);
+        decode_word(word, w, rho0, rq, bq);
     }
     // the same with the liquid fraction rounded stochastically (up with probability
     // (x - lo)/(hi - lo), rnd a uniform 32-bit number): per-step changes far below one
