@@ -541,32 +541,32 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         T ac1[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};  // shares of plane z+1
         if (active) {
             T Fi[19];
-            T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+            T rR = 0, rho = 0, jx = 0, jy = 0, jz = 0;
             const bool top_gas = z == nz - 1 && top_bc == 1;
             if constexpr (ASYNC) cp_async_wait<0>();  // plane z landed
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                // (a bounced-back element has the same weight: w_opp(i) = w_i)
-                T r, b;
+                // total F_i and f^R_i (a bounced-back element has the same weight: w_opp(i) = w_i)
+                T F, r;
                 if constexpr (ASYNC) {
                     const unsigned* st = stage_dyn + tid;
                     if constexpr (S::WORDS == 2)
-                        S::decode(__uint_as_float(st[(size_t)i * NT]), __uint_as_float(st[(size_t)(19 + i) * NT]),
-                                  (T)wq(i), rho0, r, b);
+                        S::decode_total(__uint_as_float(st[(size_t)i * NT]),
+                                        __uint_as_float(st[(size_t)(19 + i) * NT]), (T)wq(i), rho0, F, r);
                     else
-                        S::decode_word(st[(size_t)i * NT], (T)wq(i), rho0, r, b);
+                        S::decode_word_total(st[(size_t)i * NT], (T)wq(i), rho0, F, r);
                 } else {
-                    S::decode(rawR[i], rawB[i], (T)wq(i), rho0, r, b);
+                    S::decode_total(rawR[i], rawB[i], (T)wq(i), rho0, F, r);
                 }
                 if (top_gas && cz(i) < 0) {
                     // pure-gas equilibrium streams in; what streamed out is booked
                     r = T(0);
-                    b = (T)wq(i) * rho0;
-                    top_in += b;
+                    F = (T)wq(i) * rho0;
+                    top_in += F;
                 }
                 rR += r;
-                rB += b;
-                Fi[i] = r + b;
+                rho += F;
+                Fi[i] = F;
                 if constexpr (cx(i) != 0) jx += cx(i) * Fi[i];
                 if constexpr (cy(i) != 0) jy += cy(i) * Fi[i];
                 if constexpr (cz(i) != 0) jz += cz(i) * Fi[i];
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 Fy += fe[1];
                 Fz += fe[2];
             }
-            const T rho = rR + rB;
+            const T rB = rho - rR;
             if (!(rho > T(0))) err |= ERR_NAN;
             const T irho = T(1) / rho;
             const T ux = (jx + T(0.5) * Fx) * irho, uy = (jy + T(0.5) * Fy) * irho,

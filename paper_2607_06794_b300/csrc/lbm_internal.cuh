@@ -70,6 +70,11 @@ struct StoreF64 {
         r = a;
         b = c;
     }
+    // total F = f^R + f^B and f^R
+    static __device__ __forceinline__ void decode_total(E a, E c, T w, T rho0, T& F, T& r) {
+        r = a;
+        F = a + c;
+    }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
         r = __ldg(p + k);
@@ -105,6 +110,11 @@ struct StoreF32 {
     static __device__ __forceinline__ void decode(E a, E c, T w, T rho0, T& r, T& b) {
         r = a;
         b = c;
+    }
+    // total F = f^R + f^B and f^R
+    static __device__ __forceinline__ void decode_total(E a, E c, T w, T rho0, T& F, T& r) {
+        r = a;
+        F = a + c;
     }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
@@ -197,6 +207,13 @@ struct StoreShift16 {
                                                        float& b) {
         const float2 v = Cvt<H>::unpack(word);
         decode(v.x, v.y, w, rho0, r, b);
+    }
+    // total F = f^R + f^B and f^R of an element word
+    static __device__ __forceinline__ void decode_word_total(unsigned word, float w, float rho0, float& F,
+                                                             float& r) {
+        const float2 v = Cvt<H>::unpack(word);
+        F = v.x + w * rho0;
+        r = (v.y + 0.5f) * F;
     }
     static __device__ __forceinline__ void load(const E* __restrict__ p, unsigned cs, unsigned k,
                                                 T w, T rho0, T& r, T& b) {
