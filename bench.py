@@ -10,6 +10,7 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -31,8 +32,8 @@ ALG_BYTES = {"fp64": 640, "fp32": 320, "fp16": 168, "bf16": 168}
 
 # DRAM bytes (read + write) per launch of the fused kernel from one ncu capture
 # (profiles/k_stream_collide_c2_fp32.md), keyed by the hash of the kernel source
-# when they were taken and the workload; null once the source changes.
-TRAFFIC = {("030869a3eaa5", "c2_256x128x64_stripe_200wires"): 360808448 + 306302208}
+# when they were taken, the workload and the tiling; null once any of them differs.
+TRAFFIC = {("09ea0d16435d", "c2_256x128x64_stripe_200wires", 6): 362198272 + 305524224}
 
 
 def kernel_hash():
@@ -57,9 +58,35 @@ def peaks():
         return 6400.0, "fallback"
 
 
+class _Nvml:
+    """The few NVML calls the clock sampler needs, through the driver's libnvidia-ml."""
+
+    CLOCK_SM = 1
+
+    def __init__(self, bus_id=None):
+        L = ctypes.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        ok = bus_id is not None and L.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(h)) == 0
+        if not ok and L.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML device handle")
+        self.L, self.h = L, h
+        self.get_reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        cur, mx, mask = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if self.L.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, ctypes.byref(cur)) != 0:
+            return None
+        self.L.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, ctypes.byref(mx))
+        self.get_reasons(self.h, ctypes.byref(mask))
+        return cur.value, mx.value, mask.value
+
+
 class Clocks:
     """SM clocks and throttle reasons sampled during the timed region: NVML polled every
-    5 ms from a thread (nvidia-smi at 200 ms when NVML is unavailable)."""
+    5 ms from a thread (nvidia-smi every 20 ms when NVML cannot be opened)."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
@@ -70,13 +97,7 @@ class Clocks:
         self.stop_evt = threading.Event()
         self.p = None
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            try:
-                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(bus_id)
-            except Exception:
-                self.h = pynvml.nvmlDeviceGetHandleByIndex(0)
+            self.nv = _Nvml(bus_id)
             self.t = threading.Thread(target=self._poll, daemon=True)
             self.t.start()
         except Exception:
@@ -85,26 +106,28 @@ class Clocks:
             q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "20"]
             if bus_id:
                 cmd += ["-i", bus_id]
             try:
                 self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
             except Exception:
                 self.p = None
+            # start timing only once the sampler is running
+            t0 = time.time()
+            while self.p is not None and time.time() - t0 < 5.0 and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.01)
 
     def _poll(self):
-        nv = self.nv
-        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
         while not self.stop_evt.is_set():
             try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
-                self.maxes.append(nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM))
-                mask = get_reasons(self.h)
-                for name, bit in self.REASONS.items():
-                    if mask & bit:
-                        self.reasons.add(name)
+                v = self.nv.sample()
+                if v is not None:
+                    self.samples.append(v[0])
+                    self.maxes.append(v[1])
+                    for name, bit in self.REASONS.items():
+                        if v[2] & bit:
+                            self.reasons.add(name)
             except Exception:
                 pass
             self.stop_evt.wait(0.005)
@@ -138,7 +161,7 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm), "source": "nvidia-smi 200 ms"}
+                "samples": len(sm), "source": "nvidia-smi 20 ms"}
 
 
 def dist_env():
@@ -287,6 +310,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiling", type=int, default=None,
+                    help="use this candidate tiling of the fused kernel instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -314,15 +339,20 @@ def main():
     sim = make_sim(wl)
     sim.step(args.warmup)
     tuned = None
-    if not args.no_autotune:
-        # part of warm-up: real steps under each candidate tile shape
+    if args.tiling is not None:
+        sim.set_tiling(args.tiling)
+        tuned = (args.tiling, None)
+        sim.step(3)
+    elif not args.no_autotune:
+        # part of warm-up: real steps under each candidate tiling
         tuned = sim.autotune(3)
         sim.step(3)
     sim.sync()
     if pg is not None:
         pg.barrier()
     try:
-        bus = torch.cuda.get_device_properties(local).pci_bus_id
+        pr = torch.cuda.get_device_properties(local)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
     except Exception:
         bus = None
     clk = Clocks(bus)
@@ -338,7 +368,7 @@ def main():
     hbm, peak_kind = peaks()
     achieved = ALG_BYTES[prec] * wl.nodes / (ms_fluid * 1e-3) / 1e9
     kh = kernel_hash()
-    tr = TRAFFIC.get((kh, wl.name))
+    tr = TRAFFIC.get((kh, wl.name, None if tuned is None else tuned[0]))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": tr, "peak_kind": peak_kind,
                 "kernel": "k_stream_collide", "ms_per_launch": round(ms_fluid, 5),
@@ -455,7 +485,7 @@ def main():
                        "l2": "inputs larger than L2 (population buffers "
                              f"{2 * 19 * wl.nodes * {'fp64': 8, 'fp32': 4}.get(prec, 2) / 1e6:.0f} MB x2)",
                        "parallelism": f"replicas x{world}",
-                       "tile_shape": None if tuned is None else tuned[0]},
+                       "tiling": None if tuned is None else tuned[0]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * steps_done_lp, "clocks": clocks, "variants": variants,
         }

@@ -168,12 +168,31 @@ lbm_status lbm_step(lbm_handle* h, int n_steps);
 lbm_status lbm_profile_steps(lbm_handle* h, int n_steps, double* ms_fluid, double* ms_step);
 
 /* Autotuner of the fused kernel's blocking (no paper counterpart): times
- * every candidate tile shape (columns per block x z-chunk) on
- * steps_per_candidate real time steps of this batch and keeps the fastest.
- * Every candidate computes the same step, so the steps taken are ordinary
- * steps of the run.  *chosen receives the candidate index and *best_ms the
- * mean milliseconds of one fused launch (either may be NULL). */
+ * every candidate tiling (columns of nodes per block in x and y, times a
+ * z-chunk per block) on steps_per_candidate real time steps of this batch and
+ * keeps the fastest.  Every candidate computes the same step, so the steps
+ * taken are ordinary steps of the run.  *chosen receives the candidate index
+ * and *best_ms the mean milliseconds of one fused launch (either may be NULL). */
 lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, double* best_ms);
+
+/* Number of candidate tilings (no paper counterpart); a constant of the build. */
+int lbm_tiling_count(void);
+
+/* Select candidate tiling `index` (0 <= index < lbm_tiling_count()) without
+ * timing it (no paper counterpart).  Synchronises the stream and rebuilds the
+ * moments the next step reads, so the run continues unchanged.  Returns
+ * LBM_EINVAL for an index out of range. */
+lbm_status lbm_set_tiling(lbm_handle* h, int index);
+
+/* Host-only view of candidate tiling `index` for a batch (no paper
+ * counterpart; no CUDA call is made): one column piece per block of the fused
+ * kernel.  out (host, cap x 7 ints, may be NULL when cap is 0) receives per
+ * block: instance, x0, y0, z0, z1 and the piece's width and height in nodes
+ * (planes z0 <= z < z1 of the nodes x0 <= x < x0 + width, y0 <= y < y0 +
+ * height).  *n_blocks receives the number of blocks.  Returns LBM_EINVAL for
+ * a bad index or config, and LBM_ENOMEM_WS when cap is below *n_blocks (the
+ * count is still set). */
+lbm_status lbm_tiling_table(const lbm_config* cfgs, int n, int index, int* out, int cap, int* n_blocks);
 
 /* Wait for the stream and return the first latched device-side failure. */
 lbm_status lbm_sync(lbm_handle* h);

@@ -103,6 +103,26 @@ def workspace_bytes(cfgs) -> int:
     return int(_lib.load().lbm_workspace_bytes(arr, len(cfgs)))
 
 
+def tiling_count() -> int:
+    """Number of candidate tilings of the fused kernel."""
+    return int(_lib.load().lbm_tiling_count())
+
+
+def tiling_table(cfgs, index):
+    """Blocks of tiling `index` for a batch (host only): (n_blocks, 7) int array of
+    instance, x0, y0, z0, z1, width, height."""
+    L = _lib.load()
+    arr = (_lib.lbm_config * len(cfgs))(*[c.to_c() for c in cfgs])
+    nbl = C.c_int()
+    st = L.lbm_tiling_table(arr, len(cfgs), int(index), None, 0, C.byref(nbl))
+    if st not in (_lib.OK, _lib.ENOMEM_WS):
+        _check(st, "lbm_tiling_table")
+    out = np.zeros((max(nbl.value, 1), 7), np.int32)
+    _check(L.lbm_tiling_table(arr, len(cfgs), int(index), out.ctypes.data_as(C.POINTER(C.c_int)),
+                              int(nbl.value), C.byref(nbl)), "lbm_tiling_table")
+    return out[:nbl.value]
+
+
 class Simulation:
     """A batch of lattice instances advancing together on one CUDA stream."""
 
@@ -154,11 +174,19 @@ class Simulation:
         return a.value, b.value
 
     def autotune(self, steps_per_candidate=5):
-        """Pick the fastest fused-kernel tile shape on real steps; returns (index, ms)."""
+        """Pick the fastest fused-kernel tiling on real steps; returns (index, ms)."""
         k, ms = C.c_int(), C.c_double()
         _check(self.L.lbm_autotune(self.h, int(steps_per_candidate), C.byref(k), C.byref(ms)),
                "lbm_autotune")
         return k.value, ms.value
+
+    def tiling_count(self) -> int:
+        """Number of candidate tilings of the fused kernel."""
+        return int(self.L.lbm_tiling_count())
+
+    def set_tiling(self, index):
+        """Use candidate tiling `index` from the next step on (same results, other blocking)."""
+        _check(self.L.lbm_set_tiling(self.h, int(index)), "lbm_set_tiling")
 
     def sync(self):
         _check(self.L.lbm_sync(self.h), "lbm_sync")

@@ -16,7 +16,7 @@ FP64, FP32, FP16_SHIFTED, BF16_SHIFTED = range(4)
 
 # every entry point that include/lbm.h declares
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_substrate_pattern", "lbm_add_nanowires",
-           "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
+           "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_tiling_count", "lbm_set_tiling", "lbm_tiling_table", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
            "lbm_deposit_descriptors", "lbm_destroy", "lbm_status_string", "lbm_mlp_param_count",
            "lbm_mlp_scratch_bytes", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
            "lbm_deposit_descriptors_noalloc", "lbm_deposit_conductivity", "lbm_deposit_profiles",
@@ -88,6 +88,13 @@ def load():
     L.lbm_profile_steps.argtypes = [vp, C.c_int, dp, dp]
     L.lbm_autotune.restype = C.c_int
     L.lbm_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), dp]
+    L.lbm_tiling_count.restype = C.c_int
+    L.lbm_tiling_count.argtypes = []
+    L.lbm_set_tiling.restype = C.c_int
+    L.lbm_set_tiling.argtypes = [vp, C.c_int]
+    L.lbm_tiling_table.restype = C.c_int
+    L.lbm_tiling_table.argtypes = [C.POINTER(lbm_config), C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int,
+                                   C.POINTER(C.c_int)]
     L.lbm_sync.restype = C.c_int
     L.lbm_sync.argtypes = [vp]
     L.lbm_clear_error.restype = C.c_int

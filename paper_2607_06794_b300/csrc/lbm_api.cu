@@ -22,12 +22,16 @@ using namespace lbm;
 
 namespace {
 
-// Tile shapes of the fused kernel the autotuner chooses from (columns x-by-y,
-// then a z-chunk per block; chunk 0 means "split until the GPU is filled").
+// Tilings of the fused kernel the autotuner chooses from: columns of tx-by-ty
+// nodes, then a z-chunk per block (chunk 0 means "split until the whole batch
+// fills the GPU"; chunks above nz take the whole column).  Blocks of equal
+// chunks march up in step, so the halo planes a block re-reads were just read
+// by its neighbours and come from L2.
 struct Shape {
     int tx, ty, chunk;
 };
-const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {32, 4, 0}, {32, 4, 16}, {32, 4, 32}};
+const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {32, 8, 64},
+                        {32, 4, 0}, {32, 4, 16}, {32, 4, 32}, {32, 4, 64}};
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 64;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
@@ -58,6 +62,7 @@ struct Layout {
     double* stage = nullptr;
     size_t stage_bytes = 0;
     int ntiles = 0;
+    size_t tile_cap = 0;  // entries the tile table has room for
 };
 
 // neighbour-list radius: the longest interaction range plus a skin of one
@@ -72,28 +77,42 @@ double rlist_of(const lbm_config& c) {
 // planes per block: at most 240 (241 with a merged last plane) so that a chunk spans at most 32 coupling-tile
 // slabs of 8 planes (the fused kernel keeps their flags in one 32-bit mask)
 constexpr int MAX_CHUNK = 240;
-int chunk_z(const lbm_config& c, const Shape& sh) {
+// column tiles of all instances (the x-by-y tiles of the fused kernel)
+long long column_tiles(const lbm_config* cfgs, int n, const Shape& sh) {
+    long long cols = 0;
+    for (int k = 0; k < n; ++k)
+        cols += (long long)((cfgs[k].nx + sh.tx - 1) / sh.tx) * ((cfgs[k].ny + sh.ty - 1) / sh.ty);
+    return cols;
+}
+
+int chunk_z(const lbm_config& c, const Shape& sh, long long cols_all) {
     if (sh.chunk > 0) return std::max(2, std::min(std::min(sh.chunk, MAX_CHUNK), c.nz));
-    // enough blocks to fill the GPU on small lattices
+    // enough blocks over the whole batch to fill the GPU when the lattices are small
     const long long cols = (long long)((c.nx + sh.tx - 1) / sh.tx) * ((c.ny + sh.ty - 1) / sh.ty);
     int ch = std::min(c.nz, MAX_CHUNK);
-    while (cols * ((c.nz + ch - 1) / ch) < 4 * 148 && ch > 8) ch = (ch + 1) / 2;
+    while ((cols_all - cols) + cols * ((c.nz + ch - 1) / ch) < 4 * 148 && ch > 8) ch = (ch + 1) / 2;
     return std::max(2, std::min(ch, c.nz));
 }
 
+// z-ranges of the chunks of one column: never a 1-plane chunk
+std::vector<std::pair<int, int>> z_chunks(int nz, int ch) {
+    std::vector<std::pair<int, int>> zr;
+    for (int z0 = 0; z0 < nz;) {
+        int z1 = std::min(nz, z0 + ch);
+        if (nz - z1 > 0 && nz - z1 < 2) z1 = nz;
+        zr.push_back({z0, z1});
+        z0 = z1;
+    }
+    return zr;
+}
+
+// the tile table of a tiling: one column piece per block
 std::vector<TileDesc> make_tiles(const lbm_config* cfgs, int n, const Shape& sh) {
+    const long long cols_all = column_tiles(cfgs, n, sh);
     std::vector<TileDesc> t;
     for (int k = 0; k < n; ++k) {
         const lbm_config& c = cfgs[k];
-        const int ch = chunk_z(c, sh);
-        std::vector<std::pair<int, int>> zr;
-        for (int z0 = 0; z0 < c.nz;) {
-            int z1 = std::min(c.nz, z0 + ch);
-            if (c.nz - z1 > 0 && c.nz - z1 < 2) z1 = c.nz;  // never leave a 1-plane chunk
-            zr.push_back({z0, z1});
-            z0 = z1;
-        }
-        for (auto& r : zr)
+        for (auto& r : z_chunks(c.nz, chunk_z(c, sh, cols_all)))
             for (int y0 = 0; y0 < c.ny; y0 += sh.ty)
                 for (int x0 = 0; x0 < c.nx; x0 += sh.tx)
                     t.push_back(TileDesc{k, x0, y0, r.first, r.second, 0, 0, 0});
@@ -108,6 +127,7 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
     size_t maxt = 0;
     for (int k = 0; k < NSHAPES; ++k) maxt = std::max(maxt, make_tiles(cfgs, n, SHAPES[k]).size());
     L.d_tiles = (TileDesc*)cv.take(sizeof(TileDesc) * maxt);
+    L.tile_cap = maxt;
     size_t need_stage = 0;
     for (int k = 0; k < n; ++k) {
         const lbm_config& c = cfgs[k];
@@ -284,6 +304,7 @@ lbm_status launch_fused(lbm_handle* h) {
 // select a tile shape: rebuild and upload the tile table
 lbm_status set_shape(lbm_handle* h, int k) {
     std::vector<TileDesc> tiles = make_tiles(h->cfg.data(), (int)h->cfg.size(), SHAPES[k]);
+    if (tiles.size() > h->L.tile_cap || tiles.empty()) return LBM_EINVAL;
     CK(cudaMemcpyAsync(h->L.d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1021,6 +1042,37 @@ lbm_status lbm_autotune(lbm_handle* h, int steps_per_candidate, int* chosen, dou
     if (st != LBM_OK) return st;
     if (chosen) *chosen = best;
     if (best_ms) *best_ms = bt;
+    return LBM_OK;
+}
+
+int lbm_tiling_count(void) { return NSHAPES; }
+
+lbm_status lbm_set_tiling(lbm_handle* h, int index) {
+    if (!h || index < 0 || index >= NSHAPES) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(h->stream));
+    lbm_status st = set_shape(h, index);
+    for (int i = 0; st == LBM_OK && i < (int)h->cfg.size(); ++i) st = run_moments_any(h, i);
+    if (st == LBM_OK) CK(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+lbm_status lbm_tiling_table(const lbm_config* cfgs, int n, int index, int* out, int cap, int* n_blocks) {
+    if (!cfgs || n < 1 || index < 0 || index >= NSHAPES || cap < 0 || !n_blocks || (cap > 0 && !out))
+        return LBM_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        lbm_status st = check_config(cfgs[k]);
+        if (st != LBM_OK) return st;
+    }
+    const Shape& sh = SHAPES[index];
+    const std::vector<TileDesc> t = make_tiles(cfgs, n, sh);
+    *n_blocks = (int)t.size();
+    if ((size_t)cap < t.size()) return LBM_ENOMEM_WS;
+    for (size_t i = 0; i < t.size(); ++i) {
+        const lbm_config& c = cfgs[t[i].inst];
+        const int v[7] = {t[i].inst, t[i].x0, t[i].y0, t[i].z0, t[i].z1, std::min(sh.tx, c.nx - t[i].x0),
+                          std::min(sh.ty, c.ny - t[i].y0)};
+        for (int j = 0; j < 7; ++j) out[7 * i + j] = v[j];
+    }
     return LBM_OK;
 }
 
