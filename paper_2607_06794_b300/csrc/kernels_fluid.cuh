@@ -115,6 +115,13 @@ template <>
 __device__ __forceinline__ float inv_norm<float>(float g2) { return rsqrtf(g2); }
 template <>
 __device__ __forceinline__ double inv_norm<double>(double g2) { return 1.0 / sqrt(g2); }
+// smallest normal number of the compute type (below it a square is treated as zero)
+template <typename T>
+__device__ __forceinline__ constexpr T min_normal();
+template <>
+__device__ __forceinline__ constexpr float min_normal<float>() { return 1.17549435e-38f; }
+template <>
+__device__ __forceinline__ constexpr double min_normal<double>() { return 2.2250738585072014e-308; }
 
 // Liquid column height h(x,y) = sum_z (1 + C)/2 of the current moments (Eq. (8))
 // for instances whose sink is on in this step.  A block takes 32 columns with 8
@@ -613,13 +620,15 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             const T gsrc = T(1) - T(0.5) * omega;
             const T g2 = Gx * Gx + Gy * Gy + Gz * Gz;
             const bool hasg = g2 > T(1e-16);
-            const T ig = hasg ? inv_norm<T>(g2) : T(0);
-            const T gm = g2 * ig;
+            // 1/|G| wherever |G| is a normal number; the unit vector of the recolouring
+            // takes it above the threshold only, the sink takes |G| itself (Eq. (8))
+            const T ign = g2 > min_normal<T>() ? inv_norm<T>(g2) : T(0);
+            const T ig = hasg ? ign : T(0);
             const T coef = beta * (rR * rB * irho);
             T dm = 0;
             if (evap_on) {
                 const T ht = hcol * inv_h0;
-                if (ht > T(0)) dm = J0 / (Kk + ht) * T(0.5) * gm;
+                if (ht > T(0)) dm = J0 / (Kk + ht) * T(0.5) * (g2 * ign);
             }
             const T rGx = Gx * ig, rGy = Gy * ig, rGz = Gz * ig;
             const T base0 = T(1) - T(1.5) * usq;

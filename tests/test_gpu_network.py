@@ -164,6 +164,27 @@ def test_conductivity_rejects_bad_arguments(lbm):
         sim.profiles(0, 0, 0.0, 10.0, 0, 20.0, 5.0)
 
 
+def test_empty_deposits_give_zero_descriptors_network_and_profiles(lbm):
+    """A lattice with bead capacity but no wires, and one without capacity: no bonds, no
+    clusters, no current (kappa* = 0 with a converged solve), empty bins."""
+    cfgs = [lbm.Config(48, 32, 12, prec="fp32", cx=23.5, cy=15.5, cz=-0.5, a=18, b=12, c=9,
+                       max_beads=64, x_src=12.0, x_snk=36.0),
+            lbm.Config(48, 32, 12, prec="fp32", cx=23.5, cy=15.5, cz=-0.5, a=18, b=12, c=9,
+                       x_src=12.0, x_snk=36.0)]
+    sim = lbm.Simulation(cfgs)
+    sim.step(2)
+    for k in range(2):
+        d = sim.descriptors(k)
+        assert d["n_beads"] == 0 and d["n_clusters"] == 0 and d["percolates"] == 0
+        assert d["S_x"] == 0.0
+        c = sim.conductivity(k)
+        assert c["kappa"] == 0.0 and c["I_tot"] == 0.0 and c["n_edges"] == 0
+        assert c["I_ref"] == pytest.approx(1.0 / 24.0, rel=1e-15)
+        S, g, nb, nd = sim.profiles(k, 0, 0.0, 48.0, 6, 15.5, 8.0)
+        assert np.all(S == 0.0) and np.all(g == 0.0) and np.all(nb == 0) and np.all(nd == 0)
+    assert sim.status() == 0
+
+
 @pytest.mark.parametrize("axis", [0, 1])
 def test_profiles_match_oracle(lbm, net, axis):
     nx, ny = 64, 40

@@ -415,3 +415,34 @@ def test_every_tiling_matches_the_oracle_on_a_batch(lbm, oracle):
             assert a[3] == pytest.approx(acc.top_in, rel=1e-12), (t, k)
         assert np.allclose(sim.read(1, "bead_x"), ob.X, rtol=0, atol=1e-11), t
         del sim
+
+
+def test_graph_direct_and_profiled_steps_with_beads_and_sink_match_the_oracle(lbm, oracle):
+    """Graph-replayed, directly launched and profiled steps (events around the fused launch),
+    mixed in one run with beads and the evaporation sink, advance like the oracle. The sink acts
+    wherever grad C is nonzero, also in the liquid where |grad C| is below the 1e-8 threshold
+    of the interface normal (Eq. (8) takes |grad C| itself)."""
+    cfg = droplet_cfg(lbm, nx=64, ny=40, nz=20, prec="fp64", max_beads=40, xi=0.02, a=20, b=12, c=14,
+                      J0=1e-3, evap_start=0)
+    p, fR, fB, cot = oracle_state(oracle, cfg, 2)
+    fil, pos, X = bead_case(cfg, seed=53, n_fil=4)
+    cen = X.reshape(4, 4, 3).mean(axis=1)
+    dirs = X.reshape(4, 4, 3)[:, -1] - X.reshape(4, 4, 3)[:, 0]
+    sim = lbm.Simulation([cfg])
+    sim.write(0, "populations", np.stack([fR, fB]))
+    sim.add_nanowires(0, 4, 8.0, cen, dirs)
+    ob = oracle.Beads(fil, pos, sim_free_positions(cen, dirs, 4, cfg))
+    acc = oracle.Acc()
+    for _ in range(6):
+        oracle.step(p, fR, fB, cot, acc, ob)
+    sim.step(2)
+    sim.profile_steps(2)
+    sim.step(1)
+    sim.profile_steps(1)
+    sim.sync()
+    assert sim.status() == 0
+    assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-11
+    assert np.allclose(sim.read(0, "bead_x"), ob.X, rtol=0, atol=1e-11)
+    a = sim.read(0, "accum")
+    assert a[0] == 6
+    assert a[2] == pytest.approx(acc.evaporated, rel=1e-11)
