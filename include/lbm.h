@@ -204,6 +204,16 @@ lbm_status lbm_clear_error(lbm_handle* h);
  * `bytes` must equal the field's size.  Synchronises the stream. */
 lbm_status lbm_read_fields(lbm_handle* h, int inst, unsigned field, void* host_dst, size_t bytes);
 
+/* Budget record of instance `inst` without waiting (no paper counterpart; the
+ * FP64 budgets of Eq. (8) and of the top boundary, for monitoring a run step by
+ * step): host_dst (6 doubles, the layout of LBM_FIELD_ACCUM: step, h0,
+ * evaporated, top_in, top_out, n_beads) must be page-locked host memory that
+ * the caller owns; entries 1-4 are copied on the handle's stream behind the
+ * steps already enqueued and hold their values once the stream has reached the
+ * copy (after lbm_sync or any synchronising call); entries 0 and 5 are written
+ * before the call returns.  Returns LBM_EINVAL for a bad instance or NULL. */
+lbm_status lbm_read_accum_async(lbm_handle* h, int inst, double* host_dst);
+
 /* Overwrite one writable field from host memory (checkpoint restore).
  * Writing populations recomputes the derived moment buffers.  Synchronous. */
 lbm_status lbm_write_fields(lbm_handle* h, int inst, unsigned field, const void* host_src,

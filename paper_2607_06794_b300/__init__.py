@@ -229,6 +229,16 @@ class Simulation:
                f"lbm_read_fields({field})")
         return host_tensor
 
+    def read_accum_async(self, inst, host_tensor):
+        """Enqueue a copy of the budget record (the 'accum' field layout) into a pinned
+        float64 host tensor of 6; its values hold after the next sync."""
+        import torch
+        assert host_tensor.dtype == torch.float64 and host_tensor.numel() == 6 and host_tensor.is_pinned()
+        _check(self.L.lbm_read_accum_async(self.h, inst, C.cast(C.c_void_p(host_tensor.data_ptr()),
+                                                                 C.POINTER(C.c_double))),
+               "lbm_read_accum_async")
+        return host_tensor
+
     def write(self, inst, field, arr):
         shape, dt = self._shape(inst, field)
         a = np.ascontiguousarray(arr, dt).reshape(shape)

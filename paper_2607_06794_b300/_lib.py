@@ -16,7 +16,7 @@ FP64, FP32, FP16_SHIFTED, BF16_SHIFTED = range(4)
 
 # every entry point that include/lbm.h declares
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_substrate_pattern", "lbm_add_nanowires",
-           "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_tiling_count", "lbm_set_tiling", "lbm_tiling_table", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_write_fields",
+           "lbm_step", "lbm_profile_steps", "lbm_autotune", "lbm_tiling_count", "lbm_set_tiling", "lbm_tiling_table", "lbm_sync", "lbm_clear_error", "lbm_read_fields", "lbm_read_accum_async", "lbm_write_fields",
            "lbm_deposit_descriptors", "lbm_destroy", "lbm_status_string", "lbm_mlp_param_count",
            "lbm_mlp_scratch_bytes", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
            "lbm_deposit_descriptors_noalloc", "lbm_deposit_conductivity", "lbm_deposit_profiles",
@@ -99,6 +99,8 @@ def load():
     L.lbm_sync.argtypes = [vp]
     L.lbm_clear_error.restype = C.c_int
     L.lbm_clear_error.argtypes = [vp]
+    L.lbm_read_accum_async.restype = C.c_int
+    L.lbm_read_accum_async.argtypes = [vp, C.c_int, dp]
     L.lbm_read_fields.restype = C.c_int
     L.lbm_read_fields.argtypes = [vp, C.c_int, C.c_uint, vp, C.c_size_t]
     L.lbm_write_fields.restype = C.c_int

@@ -1108,6 +1108,15 @@ static size_t field_bytes(const lbm_config& c, int nb, unsigned f) {
     }
 }
 
+lbm_status lbm_read_accum_async(lbm_handle* h, int inst, double* dst) {
+    if (!valid_inst(h, inst) || !dst) return LBM_EINVAL;
+    const InstDev& I = h->L.inst[inst];
+    dst[0] = (double)h->step;
+    dst[5] = (double)I.nb;
+    CK(cudaMemcpyAsync(dst + 1, I.acc + 1, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_read_fields(lbm_handle* h, int inst, unsigned field, void* dst, size_t bytes) {
     if (!valid_inst(h, inst) || !dst) return LBM_EINVAL;
     const lbm_config& c = h->cfg[inst];

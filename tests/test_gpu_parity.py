@@ -93,6 +93,22 @@ def test_fp64_ten_steps_with_evaporation_and_budgets(lbm, oracle):
     assert a[4] == pytest.approx(acc.top_out, rel=1e-11)
 
 
+def test_async_budget_read_matches_the_blocking_read(lbm, oracle):
+    """The budget record copied behind the steps into pinned memory equals the blocking read
+    once the stream has been synchronised."""
+    import torch
+    cfg = droplet_cfg(lbm, prec="fp32", J0=2e-3, evap_start=0)
+    sim = lbm.Simulation([cfg])
+    buf = torch.zeros(6, dtype=torch.float64, pin_memory=True)
+    for _ in range(4):
+        sim.step(1)
+        sim.read_accum_async(0, buf)
+    sim.sync()
+    ref = sim.read(0, "accum")
+    assert ref[0] == 4 and ref[2] > 0
+    assert np.array_equal(buf.numpy(), ref)
+
+
 def test_fp64_moments_and_colour_match_oracle_fields(lbm, oracle):
     cfg = droplet_cfg(lbm, prec="fp64")
     sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg)
