@@ -219,12 +219,15 @@ struct StoreShift16 {
                                                 T w, T rho0, T& r, T& b) {
         decode_word(__ldg((const unsigned*)p + k), w, rho0, r, b);
     }
+    // rq, bq: what the next step's moments (colour field, column height) sum: the values
+    // before rounding; the populations themselves are the stored words, decoded at the pull
     static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         float F = r + b;
         const unsigned word = Cvt<H>::pack(F - w * rho0, F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f);
         ((unsigned*)p)[k] = word;
-        decode_word(word, w, rho0, rq, bq);
+        rq = r;
+        bq = b;
     }
     // the same with the liquid fraction rounded stochastically (up with probability
     // (x - lo)/(hi - lo), rnd a uniform 32-bit number): per-step changes far below one
@@ -240,7 +243,8 @@ struct StoreShift16 {
         unsigned word;
         memcpy(&word, h, 4);
         ((unsigned*)p)[k] = word;
-        decode(Cvt<H>::f(h[0]), Cvt<H>::f(h[1]), w, rho0, rq, bq);
+        rq = r;
+        bq = b;
     }
     static __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                   double& r, double& b) {
