@@ -329,6 +329,55 @@ def test_full_size_c2_step_in_bench_configuration(lbm, oracle):
         del sim
 
 
+def test_full_size_c4_batch_step_on_sampled_lattices(lbm, oracle):
+    """The 64-lattice FP16 batch (26.7 M nodes, 64..192 x 64 x 48) as the benchmark runs it: one
+    step of the whole batch under two tilings (whole columns, 16-plane chunks); three sampled
+    lattices (smallest, a middle one with cohesion, largest) start from oracle droplets with wires
+    placed by the test and are compared with the FP64 oracle, every population."""
+    from paper_2607_06794_b300 import workloads
+    wl = workloads.batched_c4("fp16")
+    sampled = [0, 37, 63]
+    refs, starts, placed = {}, {}, {}
+    for k in sampled:
+        cfg = wl.cfgs[k]
+        p = oracle_params(oracle, cfg)
+        fR, fB = oracle.init_droplet(p, cfg.shape, cfg.cx, cfg.cy, cfg.cz, cfg.a, cfg.b, cfg.c, cfg.width)
+        cot = oracle.cot_map(wl.thetas[k])
+        nw, length = wl.wires[k]
+        n_b = max(1, int(round(length / cfg.d0)))
+        lo = [cfg.cx - 0.5 * cfg.a, cfg.cy - 0.5 * cfg.b, 2.5]
+        hi = [cfg.cx + 0.5 * cfg.a, cfg.cy + 0.5 * cfg.b, 0.5 * cfg.c]
+        cen, dirs = inputs.random_filaments(100 + k, min(nw, 60), n_b, cfg.d0, lo, hi, min_dist=2.05)
+        fil, pos, X = inputs.straight_filaments(cen, dirs, n_b, cfg.d0)
+        ob = oracle.Beads(fil, pos, sim_free_positions(cen, dirs, n_b, cfg))
+        starts[k] = np.stack([fR, fB])
+        placed[k] = (len(cen), n_b * cfg.d0, cen, dirs)
+        acc = oracle.Acc()
+        oracle.step(p, fR, fB, cot, acc, ob)
+        refs[k] = (fR, fB, ob.X.copy(), acc)
+    # 32x4 columns: the automatic chunk (whole 48-plane columns over this batch), 16-plane chunks
+    for t in (4, 5):
+        sim = lbm.Simulation(wl.cfgs)
+        for k in range(len(wl.cfgs)):
+            sim.set_substrate_pattern(k, wl.thetas[k])
+            if k in placed:
+                sim.write(k, "populations", starts[k])
+                sim.add_nanowires(k, *placed[k])
+            else:
+                sim.add_nanowires(k, wl.wires[k][0], wl.wires[k][1], seed=wl.cfgs[k].seed)
+        sim.set_tiling(t)
+        sim.step(1)
+        sim.sync()
+        assert sim.status() == 0, t
+        for k in sampled:
+            fR, fB, Xr, acc = refs[k]
+            assert pop_err(sim.read(k, "populations"), fR, fB) < TOL["fp16"], (t, k)
+            assert np.allclose(sim.read(k, "bead_x"), Xr, rtol=0, atol=1e-3), (t, k)
+            a = sim.read(k, "accum")
+            assert a[2] == pytest.approx(acc.evaporated, rel=2e-2), (t, k)
+        del sim
+
+
 def test_large_bead_instance_uses_cell_list_and_matches_oracle(lbm, oracle):
     """More beads than one block holds: cell-list neighbour search and one launch per sub-step."""
     cfg = droplet_cfg(lbm, nx=96, ny=64, nz=24, prec="fp64", max_beads=1400, eps_coh=0.006, xi=0.02,
