@@ -33,9 +33,14 @@
  *
  * Parity status: the fluid step is pinned by closed forms and invariants
  * (Poiseuille, Laplace law, exact linear-field gradient, mass/momentum
- * conservation, hand-computed evaporation); bead forces by finite differences
- * of the energy; descriptors by hand-made configurations.  The long drying
- * trajectory of Sec. III (Fig. 2) is qualitative only: parity unpinned.
+ * conservation, hand-computed evaporation, the lattice moments of the
+ * recolouring term, a flat interface that stays flat and segregated);
+ * conservative bead forces by finite differences of the energy; the coupling
+ * stencil by exact interpolation of a linear velocity field and the first
+ * moment of the spread reaction; solvation by its exact value in a linear
+ * colour field; friction by both branches of its law at known loads;
+ * descriptors by hand-made configurations.  The long drying trajectory of
+ * Sec. III (Fig. 2) is qualitative only: parity unpinned.
  */
 #include <math.h>
 #include <stdint.h>

@@ -48,8 +48,14 @@ enum : int { ERR_NAN = 1, ERR_FENE = 2, ERR_BEAD = 4, ERR_TIMEOUT = 8, ERR_CAP =
 // WORDS = 4-byte words per element and component layout (2: two planes of
 // 4-byte values, 1: one word per element; 0: not staged in words).  load()
 // returns (f^R, f^B) in the compute type; store() writes a post-collision pair
-// and returns the values as they will be read back (quantised), so moments
-// pushed from them match the next pull exactly.
+// and returns in (rq, bq) the pair that the push of the next step's moments
+// adds up.  FP64 and FP32 store exactly, so there the pushed moments are the
+// moments of the stored populations.  The 16-bit forms return the pair before
+// rounding: the next step's colour field and column heights then differ from
+// the moments of the stored words by the rounding of those words, while the
+// populations (and hence the mass) are always the stored words.  A restore
+// from stored words rebuilds the moments from the words themselves, so a
+// restored 16-bit run continues the unbroken one only up to that rounding.
 // ---------------------------------------------------------------------------
 // 32-bit integer hash (Wellons' "lowbias32"): the counter-based uniform source
 // of the stochastic rounding below

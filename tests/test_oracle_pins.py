@@ -430,3 +430,162 @@ def test_clusters_match_networkx_on_random_configurations(oracle):
         for comp in comps:
             assert len({lab[i] for i in comp}) == 1
             assert lab[min(comp)] == min(comp)
+
+
+# ------------------------------------------------ coupling, solvation, friction, recolouring
+C19 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1],
+                [1, 0, -1], [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]], float)
+
+
+def _node_coords(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return np.stack([x, y, z], axis=-1).astype(float)  # [nz, ny, nx, 3]
+
+
+def _streams_to(field_of_position, nx, ny, nz):
+    """Post-collision populations f_i(y) = g_i(y + c_i): after the pull every interior
+    node x holds g_i(x) (Sec. II.A, Eq. (1) streaming)."""
+    P = _node_coords(nx, ny, nz)
+    return np.stack([field_of_position(i, P + C19[i]) for i in range(19)])
+
+
+def _one_bead(oracle, X, V=(0, 0, 0), F=(0, 0, 0)):
+    return oracle.Beads(np.array([0], np.int32), np.array([0], np.int32), np.array([X], float),
+                        np.array([V], float), np.array([F], float))
+
+
+def test_drag_interpolates_a_linear_velocity_field_exactly(oracle):
+    """Trilinear coupling (Sec. II.A, Ahlrichs-Duenweg drag): a bead at rest in a fluid
+    whose velocity is linear in space, u(x) = A x + b, feels exactly gamma (A X + b);
+    the reaction spread back has total -F and first moment -F (x) X, as the weights of
+    linear interpolation reproduce the position."""
+    nx, ny, nz = 12, 12, 10
+    A = np.array([[0.0011, -0.0007, 0.0005], [0.0004, 0.0009, -0.0012], [-0.0006, 0.0003, 0.0008]])
+    b = np.array([0.002, -0.001, 0.0015])
+    # single liquid component, f_i = w_i (1 + 3 c_i.u): rho = 1 and j = u at every interior node
+    fR = _streams_to(lambda i, P: W[i] * (1.0 + 3.0 * (P @ A.T + b) @ C19[i]), nx, ny, nz)
+    fR = np.ascontiguousarray(fR)
+    fB = np.zeros_like(fR)
+    p = oracle.Params(nx, ny, nz, top_bc=0, sigma=0.0, eps_s=0.0, gamma=0.7, xi=0.0, substeps=1)
+    X = np.array([5.3, 6.8, 4.35])
+    B = _one_bead(oracle, X)
+    err, fext = oracle.step(p, fR, fB, np.zeros((ny, nx)), oracle.Acc(), B, return_fext=True)
+    assert err == 0
+    want = 0.7 * (A @ X + b)
+    assert np.allclose(B.F[0], want, rtol=0, atol=1e-16)
+    assert np.abs(want).min() > 1e-4
+    P = _node_coords(nx, ny, nz).reshape(-1, 3)
+    fe = fext.reshape(-1, 3)
+    assert np.allclose(fe.sum(axis=0), -want, rtol=0, atol=1e-17)
+    assert np.allclose(P.T @ fe, -np.outer(X, want), rtol=0, atol=1e-15)
+    assert np.count_nonzero(np.abs(fe).sum(axis=1)) == 8
+
+
+def test_solvation_force_pushes_beads_up_the_colour_gradient(oracle):
+    """Solvation (Sec. II.A): F = xi grad C, towards the liquid (C = +1).  With C linear
+    in x the colour gradient is exact (G = s e_x), so a free bead feels exactly xi s e_x."""
+    nx, ny, nz = 16, 10, 10
+    s = 0.02
+    col = lambda P: s * (P[..., 0] - 7.5)
+    fR = np.ascontiguousarray(_streams_to(lambda i, P: W[i] * (1.0 + col(P)) / 2, nx, ny, nz))
+    fB = np.ascontiguousarray(_streams_to(lambda i, P: W[i] * (1.0 - col(P)) / 2, nx, ny, nz))
+    p = oracle.Params(nx, ny, nz, top_bc=0, sigma=0.0, eps_s=0.0, gamma=0.0, xi=0.6, substeps=1)
+    B = _one_bead(oracle, [7.2, 4.6, 4.3])
+    assert oracle.step(p, fR, fB, np.zeros((ny, nx)), oracle.Acc(), B) == 0
+    assert np.allclose(B.F[0], [0.6 * s, 0.0, 0.0], rtol=0, atol=1e-16)
+
+
+def test_substrate_friction_both_branches(oracle):
+    """Load-dependent friction (Sec. II.A): |F_t| = min(gamma_t |v_t|, mu N) against the
+    half-step tangential velocity, N the downward pull of adhesion and of every other force.
+    One sub-step (dt = 1, mass 1): v_h = V + F_carried / 2, the bead drifts by v_h, then
+    the force is evaluated there."""
+    n = 12
+    fR, fB = uniform_liquid(n, n, n)  # fluid at rest: u* = 0, grad C = 0
+    mu, gt = 0.5, 1.0
+
+    def run(V, F0, z=1.0, gamma=0.0):
+        p = oracle.Params(n, n, n, top_bc=0, sigma=0.0, eps_s=0.006, gamma=gamma, xi=0.0,
+                          mu=mu, gamma_t=gt, substeps=1)
+        X = np.array([5.3, 6.7, z])
+        B = _one_bead(oracle, X, V, F0)
+        assert oracle.step(p, fR.copy(), fB.copy(), np.zeros((n, n)), oracle.Acc(), B) == 0
+        vh = np.asarray(V, float) + 0.5 * np.asarray(F0, float)
+        Fc, _ = oracle.bead_conservative_forces(p, [0], [0], (X + vh)[None, :])
+        return B.F[0], vh, Fc[0, 2]
+
+    # viscous branch: gamma_t |v_h| < mu N, the force is -gamma_t v_h (not -gamma_t V)
+    F, vh, fw = run([0.0004, -0.0003, 0.0], [0.0006, 0.0002, 0.0])
+    assert fw < -1e-3 and gt * np.hypot(*vh[:2]) < mu * -fw
+    assert np.allclose(F, [-gt * vh[0], -gt * vh[1], fw], rtol=0, atol=1e-18)
+    # Coulomb branch: mu N along -v_h / |v_h|
+    F, vh, fw = run([0.02, 0.01, 0.0], [0.004, -0.002, 0.0])
+    vt = np.hypot(*vh[:2])
+    assert gt * vt > mu * -fw
+    assert np.allclose(F, [-mu * -fw * vh[0] / vt, -mu * -fw * vh[1] / vt, fw], rtol=0, atol=1e-18)
+    # a downward drag (bead rising through fluid at rest) adds to the load
+    F, vh, fw = run([0.02, 0.0, 0.001], [0.0, 0.0, 0.0], gamma=1.0)
+    N = 1.0 * vh[2] - fw
+    assert np.allclose(F, [-vh[0] - mu * N, 0.0, -vh[2] + fw], rtol=0, atol=1e-18)
+    # out of the adhesion range (2(z + 1/2) >= r_c) there is no friction at all
+    F, vh, fw = run([0.02, 0.01, 0.0], [0.0, 0.0, 0.0], z=3.0)
+    assert fw == 0.0 and np.all(F == 0.0)
+
+
+def test_recolouring_term_moments(oracle):
+    """Recolouring (Sec. II.A, Latva-Kokko/Rothman form with strength beta): against the
+    same step at beta = 0, the red populations change by d_i with d_i = -(blue change),
+    sum_i d_i = 0 (component mass) and sum_i c_i d_i = beta rho_R rho_B / rho (1 + sqrt 2)/9 n,
+    n the unit colour gradient: the lattice sum sum_i w_i c_i c_i / |c_i| is (1 + sqrt 2)/9 I."""
+    p1 = oracle.Params(20, 14, 12, top_bc=0, sigma=0.02, beta=0.7)
+    p0 = oracle.Params(20, 14, 12, top_bc=0, sigma=0.02, beta=0.0)
+    fR, fB = oracle.init_droplet(p1, 0, 9.5, 6.5, 3.0, 6, 4, 5, 2.0)
+    # give it a flow so that the collision is not trivial
+    fR *= 1.0 + 0.03 * np.sin(np.arange(19))[:, None, None, None]
+    cot = oracle.cot_map(np.full((14, 20), 75.0))
+    f = oracle.fields(p1, fR, fB, cot)
+    aR, aB, bR, bB = fR.copy(), fB.copy(), fR.copy(), fB.copy()
+    assert oracle.step(p1, aR, aB, cot, oracle.Acc()) == 0
+    assert oracle.step(p0, bR, bB, cot, oracle.Acc()) == 0
+    d = (aR - bR).reshape(19, -1)
+    assert np.allclose(aB - bB, -(aR - bR), rtol=0, atol=1e-16)
+    assert np.abs(d.sum(axis=0)).max() < 1e-16
+    G = f["G"].reshape(-1, 3)
+    g = np.linalg.norm(G, axis=1)
+    nrm = np.where(g[:, None] > 1e-8, G / np.where(g > 0, g, 1)[:, None], 0.0)
+    rR, rB = f["rhoR"].ravel(), f["rhoB"].ravel()
+    want = 0.7 * (rR * rB / (rR + rB))[:, None] * (1 + np.sqrt(2)) / 9 * nrm
+    got = (C19.T @ d).T
+    assert np.abs(want).max() > 1e-2
+    assert np.allclose(got, want, rtol=0, atol=1e-15)
+    # even moments vanish (the term is odd in c_i)
+    assert np.abs((C19[:, 0] ** 2) @ d).max() < 1e-16
+
+
+def _slab(oracle, beta, steps):
+    nx, ny, nz = 32, 4, 12
+    p = oracle.Params(nx, ny, nz, top_bc=0, sigma=0.01, beta=beta)
+    fR, fB = oracle.init_droplet(p, 1, 15.5, 1.5, 5.5, 8.0, 1e6, 1e6, 2.0)
+    cot = oracle.cot_map(np.full((ny, nx), 90.0))
+    acc = oracle.Acc()
+    for _ in range(steps):
+        assert oracle.step(p, fR, fB, cot, acc) == 0
+    return oracle.fields(p, fR, fB, cot)["C"]
+
+
+def test_flat_interface_stays_flat_and_segregated(oracle):
+    """A liquid slab across a 90 deg substrate (Sec. II.A colour-gradient model): the
+    interface stays flat and normal to the wall, C stays in [-1, 1], the bulk phases stay
+    pure under recolouring and mix without it (beta = 0)."""
+    C = _slab(oracle, 0.7, 300)
+    assert C.min() >= -1.0 - 1e-12 and C.max() <= 1.0 + 1e-12
+    assert C[:, :, 15].min() > 0.99 and C[:, :, 0].max() < -0.99
+    # interface position per plane: the C = 0 crossing on the left flank, interpolated
+    prof = C[:, 0, :16]
+    k = np.argmax(prof > 0, axis=1)
+    xs = k - 1 + (-prof[np.arange(len(k)), k - 1]) / (prof[np.arange(len(k)), k] - prof[np.arange(len(k)), k - 1])
+    assert xs.max() - xs.min() < 0.02
+    assert np.abs(C - C[:, :1, :]).max() < 1e-12  # y-invariant
+    C0 = _slab(oracle, 0.0, 300)
+    assert C0[:, :, 15].min() < 0.9  # without recolouring the components diffuse
