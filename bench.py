@@ -1,7 +1,10 @@
-"""Benchmark: MLUPS of the fused two-component D3Q19 step (fluid + filaments)
-and its fraction of the HBM roofline, on the 256x128x64 stripe droplet with
-200 nanowires (FP32 storage); FP16/BF16 shifted storage on the same workload
-as variants; the FP64 CPU oracle timed on the host cores as the baseline.
+"""Benchmark: MLUPS of the whole two-component D3Q19 step (fluid + filaments) and
+the fused fluid kernel's fraction of the HBM roofline, on the 512x256x128 lattice
+with an aspect-6 droplet on periodic stripes and 2000 nanowires (FP32 storage).
+Variants on the same lattice and wires: FP16 and BF16 shifted storage; the
+64-lattice batched sweep in FP16 and FP32; deposit analysis.  The FP64 CPU
+oracle, timed on the host cores on an x-slab of the same workload, is the
+baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -30,10 +33,10 @@ METRIC = "2-comp D3Q19 MLUPS & % HBM roofline; FP16-store+batched vs FP32 plain"
 # in FP64).
 ALG_BYTES = {"fp64": 640, "fp32": 320, "fp16": 168, "bf16": 168}
 
-# DRAM bytes (read + write) per launch of the fused kernel from one ncu capture
-# (profiles/k_stream_collide_c2_fp32.md), keyed by the hash of the kernel source
-# when they were taken, the workload and the tiling; null once any of them differs.
-TRAFFIC = {("d5f6b319206d", "c2_256x128x64_stripe_200wires", 6): 362032640 + 305745152}
+# DRAM bytes (read + write) per launch of the fused kernel from one ncu capture of
+# the committed profiles, keyed by the hash of the kernel source when they were
+# taken, the workload and the tiling; null once any of them differs.
+TRAFFIC = {}
 
 
 def kernel_hash():
@@ -85,8 +88,8 @@ class _Nvml:
 
 
 class Clocks:
-    """SM clocks and throttle reasons sampled during the timed region: NVML polled every
-    5 ms from a thread (nvidia-smi every 20 ms when NVML cannot be opened)."""
+    """SM clocks and throttle reasons sampled during a timed region: NVML polled every
+    millisecond from a thread (nvidia-smi every 20 ms when NVML cannot be opened)."""
 
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
@@ -130,7 +133,7 @@ class Clocks:
                             self.reasons.add(name)
             except Exception:
                 pass
-            self.stop_evt.wait(0.005)
+            self.stop_evt.wait(0.001)
 
     def stop(self):
         if self.nv is not None:
@@ -138,7 +141,7 @@ class Clocks:
             self.t.join()
             sm, mx = self.samples, self.maxes
             return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                    "reasons": sorted(self.reasons), "samples": len(sm), "source": "nvml 5 ms"}
+                    "reasons": sorted(self.reasons), "samples": len(sm), "source": "nvml 1 ms"}
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
         self.p.terminate()
@@ -170,6 +173,7 @@ def dist_env():
 
 
 def time_steps(sim, steps):
+    """CUDA-event time (ms) of `steps` graph-replayed steps on the handle's stream."""
     import torch
     s = sim.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -182,10 +186,37 @@ def time_steps(sim, steps):
     return e0.elapsed_time(e1)
 
 
-def make_sim(wl):
+def wire_placement(wl):
+    """Seeded straight wires inside each droplet (every bead where the initial colour
+    exceeds 0.9, i.e. inside the droplet ellipsoid scaled by 1 - atanh(0.9) width /
+    min(a, b, c)), non-overlapping: the same placement for the GPU runs and the oracle."""
+    import numpy as np
+
+    from tests import inputs
+    out = []
+    for c, w in zip(wl.cfgs, wl.wires):
+        if w is None or w[0] == 0:
+            out.append(None)
+            continue
+        nbf = max(1, int(round(w[1] / c.d0)))
+        qmax = 1.0 - np.arctanh(0.9) * c.width / min(c.a, c.b, c.c)
+        cen, dirs = inputs.wires_in_droplet(c.seed, w[0], nbf, c.d0, (c.nx, c.ny, c.nz),
+                                            (c.cx, c.cy, c.cz), (c.a, c.b, c.c), qmax)
+        if len(cen) != w[0]:
+            raise RuntimeError(f"{wl.name}: placed {len(cen)} of {w[0]} wires")
+        out.append((cen, dirs, nbf))
+    return out
+
+
+def make_sim(wl, wires):
     from paper_2607_06794_b300 import Simulation
     sim = Simulation(wl.cfgs)
-    wl.setup(sim)
+    for k, th in enumerate(wl.thetas):
+        if th is not None:
+            sim.set_substrate_pattern(k, th)
+    for k, pw in enumerate(wires):
+        if pw is not None:
+            sim.add_nanowires(k, len(pw[0]), pw[2] * wl.cfgs[k].d0, pw[0], pw[1])
     return sim
 
 
@@ -199,38 +230,69 @@ def launches_per_step(wl):
     return n
 
 
-def oracle_workload(wl, nz=None):
-    """The FP64 oracle's state for the same workload: droplet, substrate, wires
-    (seeded straight wires inside the droplet, the same count and length)."""
+def oracle_workload(wl, wires, nx_slab=None):
+    """The FP64 oracle's state for the same workload on an x-slab of nx_slab columns
+    through the droplet centre (the whole lattice when None): droplet, substrate, and
+    the wires of the GPU runs that lie inside the slab, shifted with it."""
     import numpy as np
 
     import oracle
     from tests import inputs
     c = wl.cfgs[0]
-    nz = c.nz if nz is None else nz
-    p = oracle.Params(c.nx, c.ny, nz, tau_R=c.tau_R, tau_B=c.tau_B, beta=c.beta, sigma=c.sigma,
+    w = c.nx if nx_slab is None else min(c.nx, nx_slab)
+    x0 = 0 if w == c.nx else int(round(c.cx + 0.5 - w / 2.0))
+    p = oracle.Params(w, c.ny, c.nz, tau_R=c.tau_R, tau_B=c.tau_B, beta=c.beta, sigma=c.sigma,
                       J0=c.J0, K=c.K, evap_start=c.evap_start, top_bc=c.top_bc, eps_coh=c.eps_coh,
-                      xi=c.xi, gamma=c.gamma)
-    fR, fB = oracle.init_droplet(p, c.shape, c.cx, c.cy, c.cz, c.a, c.b, min(c.c, nz - 4), c.width)
+                      xi=c.xi, gamma=c.gamma, eps_s=c.eps_s, rc=c.rc, mu=c.mu, gamma_t=c.gamma_t)
+    fR, fB = oracle.init_droplet(p, c.shape, c.cx - x0, c.cy, c.cz, c.a, c.b, c.c, c.width)
     th = wl.thetas[0] if wl.thetas[0] is not None else np.full((c.ny, c.nx), c.theta_deg)
-    cot = oracle.cot_map(th)
+    cot = oracle.cot_map(np.ascontiguousarray(th[:, x0:x0 + w]))
     beads = None
-    if wl.wires[0] is not None:
-        nw, L = wl.wires[0]
-        nb = int(round(L / c.d0))
-        lo = [c.cx - 0.6 * c.a, c.cy - 0.6 * c.b, 2.0]
-        hi = [c.cx + 0.6 * c.a, c.cy + 0.6 * c.b, min(0.6 * c.c, nz - 3.0)]
-        cen, dirs = inputs.random_filaments(c.seed, nw, nb, c.d0, lo, hi)
-        fil, pos, X = inputs.straight_filaments(cen, dirs, nb, c.d0)
-        beads = oracle.Beads(fil, pos, X)
+    if wires[0] is not None:
+        cen, dirs, nbf = wires[0]
+        fil, pos, X = inputs.straight_filaments(cen, dirs, nbf, c.d0)
+        X[:, 0] %= c.nx
+        X[:, 1] %= c.ny
+        inside = np.ones(len(cen), bool)
+        if w < c.nx:
+            xb = X[:, 0].reshape(len(cen), nbf)
+            inside = np.all((xb >= x0 + 1.0) & (xb <= x0 + w - 2.0), axis=1)
+        keep = np.repeat(inside, nbf)
+        X = X[keep] - [x0, 0.0, 0.0]
+        fil = np.repeat(np.arange(int(inside.sum()), dtype=np.int32), nbf)
+        beads = oracle.Beads(fil, pos[keep], X)
     return p, fR, fB, cot, beads
 
 
-def cpu_baseline(wl, budget_s=12.0):
-    """The FP64 oracle on the host cores on whole steps of the same workload."""
+def oracle_sample(wl, wires, seconds_per_step):
+    """Slab width whose oracle step takes about seconds_per_step on this host (measured
+    on one step of a narrow slab; the bead pair loop grows with the square of the wires)."""
     import oracle
     c = wl.cfgs[0]
-    p, fR, fB, cot, beads = oracle_workload(wl)
+    w = min(c.nx, 32)
+    p, fR, fB, cot, beads = oracle_workload(wl, wires, w)
+    acc = oracle.Acc()
+    oracle.step(p, fR, fB, cot, acc, beads)
+    t0 = time.perf_counter()
+    oracle.step(p, fR, fB, cot, acc, beads)
+    dt = time.perf_counter() - t0
+    while w < c.nx and dt * (2 * w / 32) ** 2 <= seconds_per_step * 0.8:
+        w *= 2
+    return min(w, c.nx)
+
+
+def oracle_desc(wl, p, beads):
+    c = wl.cfgs[0]
+    return (f"{p.nx}x{p.ny}x{p.nz} x-slab of the {wl.name} lattice ({c.nx}x{c.ny}x{c.nz}) "
+            f"through the droplet centre with the {0 if beads is None else beads.n} beads of the "
+            f"GPU run's wires that lie in it")
+
+
+def cpu_baseline(wl, wires, budget_s=12.0):
+    """The FP64 oracle on the host cores: whole steps on an x-slab of the same workload."""
+    import oracle
+    w = oracle_sample(wl, wires, budget_s / 6.0)
+    p, fR, fB, cot, beads = oracle_workload(wl, wires, w)
     acc = oracle.Acc()
     oracle.step(p, fR, fB, cot, acc, beads)  # first step: page-in, not timed
     n, t0 = 0, time.perf_counter()
@@ -239,26 +301,22 @@ def cpu_baseline(wl, budget_s=12.0):
         n += 1
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(c.nx * c.ny * c.nz * n / dt / 1e6, 4), "unit": "MLUPS", "cores": cores,
-            "kind": "oracle",
-            "sample": f"{n} whole FP64 steps of the {wl.name} lattice ({c.nx}x{c.ny}x{c.nz}, "
-                      f"{0 if beads is None else beads.n} beads) after one untimed step"}
+    return {"value": round(p.nx * p.ny * p.nz * n / dt / 1e6, 4), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle", "sample": f"{n} whole FP64 steps of the {oracle_desc(wl, p, beads)}, "
+                                        f"after one untimed step"}
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle itself on the host cores, same workload and metric."""
+    """Reference arm: the FP64 oracle itself on the host cores, same workload and metric,
+    each step a whole oracle step on an x-slab sized so that K + W steps take ~2.5 minutes."""
     if rank != 0:
         return
     import oracle
     from paper_2607_06794_b300 import workloads
     wl = workloads.WORKLOADS[args.workload]()
-    c = wl.cfgs[0]
-    # each step is one whole oracle step of the workload; crop z so K+W steps stay ~3 minutes
-    per_step = c.nx * c.ny * c.nz / 4.0e6
-    nz = c.nz
-    if (args.steps + args.warmup) * per_step > 180.0:
-        nz = max(8, int(c.nz * 180.0 / ((args.steps + args.warmup) * per_step)))
-    p, fR, fB, cot, beads = oracle_workload(wl, nz)
+    wires = wire_placement(wl)
+    w = oracle_sample(wl, wires, 150.0 / (args.steps + args.warmup))
+    p, fR, fB, cot, beads = oracle_workload(wl, wires, w)
     acc = oracle.Acc()
     for _ in range(args.warmup):
         oracle.step(p, fR, fB, cot, acc, beads)
@@ -266,18 +324,17 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         oracle.step(p, fR, fB, cot, acc, beads)
     dt = time.perf_counter() - t0
-    mlups = c.nx * c.ny * nz * args.steps / dt / 1e6
+    mlups = p.nx * p.ny * p.nz * args.steps / dt / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = (f"whole FP64 oracle steps of {c.nx}x{c.ny}x{nz} (the {wl.name} droplet, "
-              f"{0 if beads is None else beads.n} beads)")
+    c = wl.cfgs[0]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "lattice": [c.nx, c.ny, nz]},
+        "config": {"workload": wl.name, "lattice": [c.nx, c.ny, c.nz], "sample_lattice": [p.nx, p.ny, p.nz]},
         "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": "whole FP64 oracle steps of the " + oracle_desc(wl, p, beads)},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -298,13 +355,47 @@ def whole_job_mlups(nodes_per_rank, steps, ms_max, world):
     return world * nodes_per_rank * steps / (ms_max * 1e-3) / 1e6
 
 
+def job_throughput(ms_local, nodes_per_rank, steps, world, pg, device):
+    """(slowest rank's ms, whole-job MLUPS) from this rank's timed region of `steps` steps
+    over its replica of nodes_per_rank nodes: the replicas exchange nothing, only this
+    maximum (and the barriers around the timed region)."""
+    ms = reduce_max(ms_local, pg, device)
+    return ms, whole_job_mlups(nodes_per_rank, steps, ms, world)
+
+
+def prepared(wl, wires, args, candidates=3):
+    """A simulation after W warm-up steps and the autotuner's trial steps (or a fixed tiling)."""
+    sim = make_sim(wl, wires)
+    sim.step(args.warmup)
+    tuned = None
+    if args.tiling is not None:
+        sim.set_tiling(args.tiling)
+        tuned = (args.tiling, None)
+        sim.step(3)
+    elif not args.no_autotune:
+        tuned = sim.autotune(candidates)
+        sim.step(3)
+    sim.sync()
+    return sim, tuned
+
+
+def clock_window(sim, ms_step, bus, min_ms=200.0):
+    """Steps for at least min_ms with the clocks sampled: MLUPS tied to the SM clock
+    when the K timed steps are too short for many clock samples."""
+    n = max(1, int(min_ms / max(ms_step, 1e-3)) + 1)
+    clk = Clocks(bus)
+    ms = time_steps(sim, n)
+    c = clk.stop()
+    return n, ms, c
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c5")
     ap.add_argument("--prec", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -319,7 +410,6 @@ def main():
         run_reference(args, rank, world)
         return
 
-    import numpy as np
     import torch
 
     from paper_2607_06794_b300 import workloads
@@ -334,20 +424,10 @@ def main():
         return reduce_max(v, pg, "cuda")
 
     mk = workloads.WORKLOADS[args.workload]
-    wl = mk(args.prec) if args.prec else mk()
+    wl = mk(args.prec) if args.prec else mk("fp32") if args.workload in ("c5", "c4") else mk()
     prec = wl.cfgs[0].prec
-    sim = make_sim(wl)
-    sim.step(args.warmup)
-    tuned = None
-    if args.tiling is not None:
-        sim.set_tiling(args.tiling)
-        tuned = (args.tiling, None)
-        sim.step(3)
-    elif not args.no_autotune:
-        # part of warm-up: real steps under each candidate tiling
-        tuned = sim.autotune(3)
-        sim.step(3)
-    sim.sync()
+    wires = wire_placement(wl)
+    sim, tuned = prepared(wl, wires, args)
     if pg is not None:
         pg.barrier()
     try:
@@ -358,9 +438,10 @@ def main():
     clk = Clocks(bus)
     ms = time_steps(sim, args.steps)
     clocks = clk.stop()
-    ms = barrier_max(ms)
+    if pg is not None:
+        pg.barrier()
+    ms, value = job_throughput(ms, wl.nodes, args.steps, world, pg, "cuda")
     ms_step = ms / args.steps
-    value = whole_job_mlups(wl.nodes, args.steps, ms, world)
 
     # roofline of the fused fluid kernel: CUDA events around every launch
     ms_fluid, ms_prof_step = sim.profile_steps(args.steps)
@@ -374,6 +455,11 @@ def main():
                 "kernel": "k_stream_collide", "ms_per_launch": round(ms_fluid, 5),
                 "alg_bytes_per_node": ALG_BYTES[prec], "kernel_src": kh,
                 "ms_per_step_direct_launch": round(ms_prof_step, 5)}
+    cw_n, cw_ms, cw_clk = clock_window(sim, ms_step, bus)
+    cwin = {"steps": cw_n, "ms_per_step": round(cw_ms / cw_n, 5),
+            "value": round(world * wl.nodes * cw_n / (cw_ms * 1e-3) / 1e6, 1), **cw_clk}
+    if cw_clk.get("sm_mhz"):
+        cwin["ms_x_mhz_per_step"] = round(cw_ms / cw_n * cw_clk["sm_mhz"], 2)
     sim.sync()
 
     # end to end through the public API with host buffers
@@ -384,8 +470,9 @@ def main():
         sim.read_into(0, "populations", pops)
         accb = torch.empty(6, dtype=torch.float64, pin_memory=True)
         colb = torch.empty((c.nz, c.ny, c.nx), dtype=torch.float64, pin_memory=True)
-        # every step: one step, then its budget record copied to pinned host memory
-        # behind it on the stream (the host does not wait); the colour field at the end
+        # the state uploaded once, then every step: one step and its budget record copied to
+        # pinned host memory behind it on the stream (the host does not wait); the colour
+        # field read at the end
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.write_from(0, "populations", pops)
@@ -405,56 +492,52 @@ def main():
         ds = barrier_max(time.perf_counter() - t1)
         e2e = {"value": round(world * wl.nodes * args.steps / dt / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": int(pops.numel() * 8 // args.steps),
-               "d2h_bytes_per_step": int(32 + colb.numel() * 8 // args.steps),
-               "blocking_read_value": round(world * wl.nodes * args.steps / ds / 1e6, 2)}
-    steps_done_lp = launches_per_step(wl)
+               "d2h_bytes_per_step": int(48 + colb.numel() * 8 // args.steps),
+               "blocking_read_value": round(world * wl.nodes * args.steps / ds / 1e6, 2),
+               "what": "FP64 state uploaded once, K steps each with its budget record read back "
+                       "asynchronously, colour field read at the end"}
+        del pops, colb
+    steps_lp = launches_per_step(wl)
     sim.close()
     del sim
     torch.cuda.empty_cache()
 
-    variants = {}
-    if not args.no_variants and args.workload == "c2" and args.prec is None:
-        for vp in ("fp16", "bf16"):
-            w2 = workloads.droplet_c2(vp)
-            s2 = make_sim(w2)
-            s2.step(args.warmup)
-            if not args.no_autotune:
-                s2.autotune(3)
-                s2.step(3)
-            s2.sync()
-            m2 = barrier_max(time_steps(s2, args.steps))
-            f2, _ = s2.profile_steps(args.steps)
-            mlups2 = world * w2.nodes * args.steps / (m2 * 1e-3) / 1e6
-            ach2 = ALG_BYTES[vp] * w2.nodes / (f2 * 1e-3) / 1e9
-            variants[vp] = {"value": round(mlups2, 1), "unit": "MLUPS",
-                            "speedup_vs_fp32": round(mlups2 / value, 3),
-                            "fluid_kernel_GBps": round(ach2, 1), "frac": round(ach2 / hbm, 4),
-                            "ms_per_step": round(m2 / args.steps, 5)}
-            s2.close()
-            del s2
-            torch.cuda.empty_cache()
-
-    if not args.no_variants and args.workload == "c2" and args.prec is None:
-        # the batched sweep: 64 uneven lattices with wires, FP16 shifted storage, one launch per step
-        w4 = workloads.batched_c4("fp16")
-        s4 = make_sim(w4)
-        s4.step(args.warmup)
-        if not args.no_autotune:
-            s4.autotune(2)
-            s4.step(2)
-        s4.sync()
-        k4 = max(20, args.steps // 4)
-        m4 = barrier_max(time_steps(s4, k4))
-        mlups4 = world * w4.nodes * k4 / (m4 * 1e-3) / 1e6
-        variants["fp16_batched_c4"] = {"value": round(mlups4, 1), "unit": "MLUPS",
-                                       "speedup_vs_fp32": round(mlups4 / value, 3),
-                                       "instances": len(w4.cfgs), "nodes": w4.nodes,
-                                       "beads": int(sum(s4.nb)), "ms_per_step": round(m4 / k4, 5)}
-        s4.close()
-        del s4
+    def measure(w2, wires2, k):
+        s2, _ = prepared(w2, wires2, args)
+        m2 = barrier_max(time_steps(s2, k))
+        f2, _ = s2.profile_steps(k)
+        out = {"value": round(world * w2.nodes * k / (m2 * 1e-3) / 1e6, 1), "unit": "MLUPS",
+               "ms_per_step": round(m2 / k, 5), "fluid_kernel_ms": round(f2, 5)}
+        p2 = w2.cfgs[0].prec
+        out["fluid_kernel_GBps"] = round(ALG_BYTES[p2] * w2.nodes / (f2 * 1e-3) / 1e9, 1)
+        out["frac"] = round(out["fluid_kernel_GBps"] / hbm, 4)
+        s2.close()
+        del s2
         torch.cuda.empty_cache()
+        return out
 
-    if not args.no_variants and args.workload == "c2" and args.prec is None:
+    variants = {}
+    default_run = args.workload == "c5" and args.prec is None
+    if not args.no_variants and default_run:
+        # 16-bit shifted storage on the same lattice with the same wires
+        for vp in ("fp16", "bf16"):
+            v = measure(workloads.droplet_c5(vp), wires, args.steps)
+            v["speedup_vs_fp32_same_workload"] = round(v["value"] / value, 3)
+            variants[vp] = v
+        # the batched sweep: 64 uneven lattices with wires, one launch per step, FP16 and FP32
+        k4 = max(20, args.steps // 4)
+        c4 = {}
+        for vp in ("fp16", "fp32"):
+            w4 = workloads.batched_c4(vp)
+            c4[vp] = measure(w4, wire_placement(w4), k4)
+        c4["fp16"]["speedup_vs_fp32_same_workload"] = round(c4["fp16"]["value"] / c4["fp32"]["value"], 3)
+        c4["instances"], c4["nodes"] = len(w4.cfgs), w4.nodes
+        variants["c4_batched"] = c4
+        # the smaller 256x128x64 stripe droplet with 200 wires, FP32
+        w2 = workloads.droplet_c2("fp32")
+        variants["c2_fp32"] = measure(w2, wire_placement(w2), args.steps)
+
+    if not args.no_variants and default_run:
         # deposit analysis of Sec. II.B on the c5 wire load (16,000 beads): Kirchhoff network
         # (FP64 CG, one block) and the axial profiles; synchronous calls, wall-clock timed
         from paper_2607_06794_b300 import Simulation
@@ -482,7 +565,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
+        cpu = cpu_baseline(wl, wires)
 
     if rank == 0:
         c = wl.cfgs[0]
@@ -499,7 +582,8 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "tiling": None if tuned is None else tuned[0]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * steps_done_lp, "clocks": clocks, "variants": variants,
+            "gpu_launches": args.steps * steps_lp, "clocks": clocks, "clock_window": cwin,
+            "variants": variants,
         }
         print(json.dumps(out), flush=True)
     if pg is not None:

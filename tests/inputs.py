@@ -70,3 +70,54 @@ def flat_deposit(seed, n_fil, n_beads, box, z=1.0, spread=0.6, spacing=2.0):
     dirs = np.c_[np.cos(ang), np.sin(ang), np.zeros(n_fil)]
     fil, pos, X = straight_filaments(cen, dirs, n_beads, spacing)
     return cen, dirs, fil, pos, X
+
+
+_PLACE = None
+
+
+def _place_lib():
+    """The placement loop in C (tests/place_wires.c), built with gcc on first use."""
+    global _PLACE
+    if _PLACE is None:
+        import ctypes as C
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src, lib = os.path.join(here, "place_wires.c"), os.path.join(here, "libplace_wires.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", lib, src, "-lm"])
+        L = C.CDLL(lib)
+        dp = C.POINTER(C.c_double)
+        L.place_wires.restype = C.c_int
+        L.place_wires.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                  dp, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  C.c_longlong, dp, dp]
+        _PLACE = L
+    return _PLACE
+
+
+def wires_in_droplet(seed, n_wires, n_beads, spacing, lattice, centre, semi_axes, q_max,
+                     min_dist=2.0, z_range=None, max_tries=None):
+    """Straight wires placed at random (uniform centres, isotropic directions) with every
+    bead inside the ellipsoid of `semi_axes` about `centre` scaled by q_max (ellipsoidal
+    radius q < q_max, minimum image in x and y), beads of different wires further apart
+    than `min_dist`, beads in z_range (default 1 <= z <= nz - 2).  Candidates are taken
+    in order, each against every wire accepted before it.  Positions wrap in x and y.
+    Returns centres (unwrapped) and unit directions, [n, 3] each (fewer rows when the
+    droplet is full before max_tries candidates)."""
+    import ctypes as C
+    nx, ny, nz = lattice
+    zlo, zhi = (1.0, nz - 2.0) if z_range is None else z_range
+    c = np.ascontiguousarray(centre, np.float64)
+    ax = np.ascontiguousarray(semi_axes, np.float64)
+    cen = np.zeros((n_wires, 3))
+    dr = np.zeros((n_wires, 3))
+    dp = C.POINTER(C.c_double)
+    lim = 200000 + 2000 * n_wires if max_tries is None else max_tries
+    got = _place_lib().place_wires(int(seed), n_wires, n_beads, float(spacing), nx, ny, nz,
+                                   c.ctypes.data_as(dp), ax.ctypes.data_as(dp), float(q_max),
+                                   float(min_dist), float(zlo), float(zhi), int(lim),
+                                   cen.ctypes.data_as(dp), dr.ctypes.data_as(dp))
+    if got < 0:
+        raise RuntimeError("wire placement: cell overflow")
+    return cen[:got], dr[:got]
