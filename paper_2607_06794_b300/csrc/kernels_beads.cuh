@@ -10,7 +10,7 @@
 namespace lbm {
 
 // beads a neighbour-search cell can hold (cells are at least rlist wide)
-constexpr int CELL_CAP = 32;
+constexpr int CELL_CAP = 64;
 
 // minimum image of a separation of two wrapped coordinates (|d| <= L)
 __device__ __forceinline__ double min_image(double d, int L) {

@@ -155,8 +155,10 @@ __global__ void __launch_bounds__(HCOL_X * HCOL_Z) k_column_height(const InstDev
     }
 }
 
-template <class S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * TY)) : 1)
+// MINB: resident blocks per SM the register budget is sized for (4 blocks of 128
+// threads: 128 registers a thread; 5 blocks: 96), a choice of the tiling autotuner
+template <class S, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
     k_stream_collide(const InstDev* __restrict__ insts, const TileDesc* __restrict__ tiles,
                      StepGlobals* __restrict__ glob) {
     using T = typename S::T;
@@ -469,24 +471,27 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const unsigned rowm = (unsigned)ym * nx, row0 = (unsigned)y * nx, rowp = (unsigned)yp * nx;
 
-    // element of direction i that streams into this thread's node of plane z
-    auto pull_index = [&](int z, int i) -> unsigned {
-        const unsigned node = (unsigned)z * nxy + row0 + x;
+    // element of direction i that streams into this thread's node of plane z; EDGE:
+    // z may be the bottom or the top plane (interior planes need no boundary test)
+    auto pull_index = [&](int z, int i, auto EDGE_) -> unsigned {
         const int sz = z - cz(i);
-        if (sz < 0 || (sz >= nz && top_bc == 0)) return (unsigned)opp(i) * N + node;  // bounce-back
-        if (sz >= nz) return (unsigned)i * N + node;  // replaced by the gas inflow
+        if constexpr (decltype(EDGE_)::value) {
+            const unsigned node = (unsigned)z * nxy + row0 + x;
+            if (sz < 0 || (sz >= nz && top_bc == 0)) return (unsigned)opp(i) * N + node;  // bounce-back
+            if (sz >= nz) return (unsigned)i * N + node;  // replaced by the gas inflow
+        }
         const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
         const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
         return (unsigned)i * N + (unsigned)sz * nxy + row + sx;
     };
     // asynchronous pull of plane z into the stage (one commit group per plane);
     // every slot is read and written by its own thread only
-    auto issue_pull = [&](int z) {
+    auto issue_pull_t = [&](int z, auto EDGE_) {
         if (active && z < z1) {
             unsigned* st = stage_dyn + tid;
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                const unsigned k = pull_index(z, i);
+                const unsigned k = pull_index(z, i, EDGE_);
                 if constexpr (S::WORDS == 2) {
                     cp_async4(st + (size_t)i * NT, src + k);
                     cp_async4(st + (size_t)(19 + i) * NT, src + cs + k);
@@ -496,6 +501,12 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
             });
         }
         cp_async_commit();
+    };
+    auto issue_pull = [&](int z) {
+        if (z == 0 || z == nz - 1)
+            issue_pull_t(z, std::true_type{});
+        else
+            issue_pull_t(z, std::false_type{});
     };
 
     // ---- prologue: C planes and normals below the first plane ----
@@ -532,7 +543,7 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         } else if (active) {
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                const unsigned k = pull_index(z, i);
+                const unsigned k = pull_index(z, i, std::true_type{});
                 rawR[i] = __ldg(src + k);
                 rawB[i] = __ldg(src + cs + k);
             });
@@ -546,10 +557,12 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
         __syncthreads();
         // ---- phase 3: decode, collide, recolour, evaporate, store, push ----
         T ac1[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};  // shares of plane z+1
-        if (active) {
+        // EDGE: the bottom or the top plane, where streaming meets the walls or the gas
+        auto phase3 = [&](auto EDGE_) {
+            constexpr bool EDGE = decltype(EDGE_)::value;
             T Fi[19];
             T rR = 0, rho = 0, jx = 0, jy = 0, jz = 0;
-            const bool top_gas = z == nz - 1 && top_bc == 1;
+            const bool top_gas = EDGE && z == nz - 1 && top_bc == 1;
             if constexpr (ASYNC) cp_async_wait<0>();  // plane z landed
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
@@ -657,10 +670,10 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 else
                     S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
                 const int tz = z + cz(i);  // the same for the whole block
-                if (tz < 0 || (tz >= nz && top_bc == 0)) {
+                if (EDGE && (tz < 0 || (tz >= nz && top_bc == 0))) {
                     ac0[1][0] += rq;  // bounces back to this node
                     ac0[1][1] += bq;
-                } else if (tz < nz) {
+                } else if (!EDGE || tz < nz) {
                     constexpr int d = cy(i) + 1;
                     T vr = rq, vb = bq;
                     if constexpr (cx(i) != 0) {
@@ -725,6 +738,12 @@ __global__ void __launch_bounds__(TX * TY, (512 / (TX * TY)) > 0 ? (512 / (TX * 
                 });
                 ac0[1][1] += inB;
             }
+        };
+        if (active) {
+            if (z == 0 || z == nz - 1)
+                phase3(std::true_type{});
+            else
+                phase3(std::false_type{});
         }
         retire(ac1);
         if constexpr (ASYNC) issue_pull(z + 1);  // its slots were consumed above by this thread

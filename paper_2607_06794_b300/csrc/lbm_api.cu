@@ -24,16 +24,19 @@ namespace {
 
 // Tilings of the fused kernel the autotuner chooses from: columns of tx-by-ty
 // nodes, then a z-chunk per block (chunk 0 means "split until the whole batch
-// fills the GPU"; chunks above nz take the whole column).  Blocks of equal
-// chunks march up in step, so the halo planes a block re-reads were just read
-// by its neighbours and come from L2.
+// fills the GPU"; chunks above nz take the whole column), and the register
+// budget as resident blocks per SM (128 registers a thread: 4 blocks of 32x4,
+// 2 of 32x8; a 96-register form of 32x4 at 5 blocks per SM measured 5-40 %
+// slower on every workload and was dropped).  Blocks of equal chunks march up
+// in step, so the halo planes a block re-reads were just read by its
+// neighbours and come from L2.
 struct Shape {
-    int tx, ty, chunk;
+    int tx, ty, chunk, minb;
 };
-const Shape SHAPES[] = {{32, 8, 0}, {32, 8, 16}, {32, 8, 32}, {32, 8, 64},
-                        {32, 4, 0}, {32, 4, 16}, {32, 4, 32}, {32, 4, 64}};
+const Shape SHAPES[] = {{32, 8, 0, 2}, {32, 8, 16, 2}, {32, 8, 32, 2}, {32, 8, 64, 2},
+                        {32, 4, 0, 4}, {32, 4, 16, 4}, {32, 4, 32, 4}, {32, 4, 64, 4}};
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
-constexpr int MAX_NBR = 64;
+constexpr int MAX_NBR = 128;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
 constexpr int PROFILE_MAX_BINS = 65536;
 
@@ -179,7 +182,7 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.ccount = (int*)cv.take(sizeof(int) * ncell);
             I.cbeads = (int*)cv.take(sizeof(int) * ncell * CELL_CAP);
             I.bxf = (float*)cv.take(sizeof(float) * 3 * (size_t)c.max_beads);
-            I.max_edges = 8 * c.max_beads + 64;
+            I.max_edges = 16 * c.max_beads + 64;
             I.edges = (int2*)cv.take(sizeof(int2) * (size_t)I.max_edges);
             I.nedges = (int*)cv.take(sizeof(int));
             I.net = (double*)cv.take(sizeof(double) * 6 * (size_t)c.max_beads);
@@ -269,19 +272,20 @@ constexpr size_t stage_bytes(int nt) {
     return (size_t)19 * S::WORDS * nt * 4;
 }
 
-template <class S, int TX, int TY>
+template <class S, int TX, int TY, int MINB>
 lbm_status prepare_one() {
     const size_t dyn = stage_bytes<S>(TX * TY);
     if (dyn > 0)
-        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dyn));
     return LBM_OK;
 }
 
 // per-kernel attributes, set once before any launch or capture
 template <class S>
 lbm_status prepare_fused() {
-    lbm_status st = prepare_one<S, 32, 8>();
-    if (st == LBM_OK) st = prepare_one<S, 32, 4>();
+    lbm_status st = prepare_one<S, 32, 8, 2>();
+    if (st == LBM_OK) st = prepare_one<S, 32, 4, 4>();
     return st;
 }
 
@@ -291,10 +295,10 @@ lbm_status launch_fused(lbm_handle* h) {
     const int nb = h->L.ntiles;
     const InstDev* in = h->L.d_inst;
     const TileDesc* td = h->L.d_tiles;
-    if (sh.tx == 32 && sh.ty == 8)
-        k_stream_collide<S, 32, 8><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
-    else if (sh.tx == 32 && sh.ty == 4)
-        k_stream_collide<S, 32, 4><<<nb, 128, stage_bytes<S>(128), h->stream>>>(in, td, h->L.glob);
+    if (sh.tx == 32 && sh.ty == 8 && sh.minb == 2)
+        k_stream_collide<S, 32, 8, 2><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
+    else if (sh.tx == 32 && sh.ty == 4 && sh.minb == 4)
+        k_stream_collide<S, 32, 4, 4><<<nb, 128, stage_bytes<S>(128), h->stream>>>(in, td, h->L.glob);
     else
         return LBM_EINVAL;
     CK(cudaGetLastError());

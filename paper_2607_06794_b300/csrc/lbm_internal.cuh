@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <cstring>
+#include <type_traits>
 
 namespace lbm {
 
@@ -151,8 +152,11 @@ struct StoreF32 {
 };
 
 // Shifted 16-bit storage: comp 0 holds F_i - w_i rho0 (total population as a
-// deviation from rest), comp 1 holds f^R_i/F_i - 1/2 (liquid fraction; exactly
-// +-1/2 in pure phases).  H is __half or __nv_bfloat16.
+// deviation from rest) in HP, comp 1 holds f^R_i/F_i - 1/2 (liquid fraction;
+// exactly +-1/2 in pure phases) in HQ.  FP16 storage keeps both halves in
+// __half; BF16 storage keeps the deviation in __nv_bfloat16 and the fraction,
+// bounded by 1/2, in __half, whose 10 fraction bits resolve it 8 times finer
+// than bfloat16's 7 (bfloat16's exponent range is of no use to a bounded number).
 template <class H>
 struct Cvt;
 template <>
@@ -175,6 +179,11 @@ struct Cvt<__half> {
         memcpy(&v, &w, 4);
         return __half22float2(v);
     }
+    // one value as the bits of a half-word and back
+    static __device__ __forceinline__ unsigned bits(float f) { return __half_as_ushort(__float2half_rn(f)); }
+    static __device__ __forceinline__ float from_bits(unsigned b) {
+        return __half2float(__ushort_as_half((unsigned short)b));
+    }
 };
 template <>
 struct Cvt<__nv_bfloat16> {
@@ -195,12 +204,34 @@ struct Cvt<__nv_bfloat16> {
         memcpy(&v, &w, 4);
         return __bfloat1622float2(v);
     }
+    static __device__ __forceinline__ unsigned bits(float f) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+    }
+    static __device__ __forceinline__ float from_bits(unsigned b) { return __uint_as_float(b << 16); }
 };
 
-template <class H>
+// the element word of an (HP, HQ) pair: HP in the low half, HQ in the high half
+template <class HP, class HQ>
+struct Pair16 {
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        if constexpr (std::is_same<HP, HQ>::value)
+            return Cvt<HP>::pack(lo, hi);
+        else
+            return Cvt<HP>::bits(lo) | (Cvt<HQ>::bits(hi) << 16);
+    }
+    static __device__ __forceinline__ float2 unpack(unsigned w) {
+        if constexpr (std::is_same<HP, HQ>::value)
+            return Cvt<HP>::unpack(w);
+        else
+            return make_float2(Cvt<HP>::from_bits(w & 0xffffu), Cvt<HQ>::from_bits(w >> 16));
+    }
+};
+
+template <class HP, class HQ>
 struct StoreShift16 {
     using T = float;
-    using E = H;
+    using E = HP;  // half-words: the deviation (HP) at even, the fraction (HQ) at odd positions
+    using H = HQ;
     static constexpr int WORDS = 1;
     static __host__ __device__ __forceinline__ void decode(float P, float psi, float w, float rho0,
                                                            float& r, float& b) {
@@ -211,13 +242,13 @@ struct StoreShift16 {
     // one element as its 4-byte word: low half P, high half psi
     static __device__ __forceinline__ void decode_word(unsigned word, float w, float rho0, float& r,
                                                        float& b) {
-        const float2 v = Cvt<H>::unpack(word);
+        const float2 v = Pair16<HP, HQ>::unpack(word);
         decode(v.x, v.y, w, rho0, r, b);
     }
     // total F = f^R + f^B and f^R of an element word
     static __device__ __forceinline__ void decode_word_total(unsigned word, float w, float rho0, float& F,
                                                              float& r) {
-        const float2 v = Cvt<H>::unpack(word);
+        const float2 v = Pair16<HP, HQ>::unpack(word);
         F = v.x + w * rho0;
         r = (v.y + 0.5f) * F;
     }
@@ -230,7 +261,7 @@ struct StoreShift16 {
     static __device__ __forceinline__ void store(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                  T rho0, T r, T b, T& rq, T& bq) {
         float F = r + b;
-        const unsigned word = Cvt<H>::pack(F - w * rho0, F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f);
+        const unsigned word = Pair16<HP, HQ>::pack(F - w * rho0, F != 0.0f ? __fdividef(r, F) - 0.5f : 0.0f);
         ((unsigned*)p)[k] = word;
         rq = r;
         bq = b;
@@ -245,9 +276,8 @@ struct StoreShift16 {
         const H lo = Cvt<H>::rd(x), hi = Cvt<H>::ru(x);
         const float flo = Cvt<H>::f(lo), fhi = Cvt<H>::f(hi);
         const float u = (float)(rnd >> 8) * (1.0f / 16777216.0f);
-        H h[2] = {Cvt<H>::h(F - w * rho0), (u * (fhi - flo) < x - flo) ? hi : lo};
-        unsigned word;
-        memcpy(&word, h, 4);
+        const H q = (u * (fhi - flo) < x - flo) ? hi : lo;
+        const unsigned word = Cvt<HP>::bits(F - w * rho0) | ((unsigned)__half_as_ushort(q) << 16);
         ((unsigned*)p)[k] = word;
         rq = r;
         bq = b;
@@ -255,19 +285,20 @@ struct StoreShift16 {
     static __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                   double& r, double& b) {
         float rr, bb;
-        decode(Cvt<H>::f(p[2 * k]), Cvt<H>::f(p[2 * k + 1]), (float)wq(i), (float)rho0, rr, bb);
+        const unsigned w = ((const unsigned*)p)[k];
+        decode(Cvt<HP>::from_bits(w & 0xffffu), Cvt<HQ>::from_bits(w >> 16), (float)wq(i), (float)rho0, rr, bb);
         r = rr;
         b = bb;
     }
     static __device__ void from_f64(E* p, long long cs, long long k, int i, double rho0, double r,
                                     double b) {
         float F = (float)(r + b);
-        p[2 * k] = Cvt<H>::h(F - (float)wq(i) * (float)rho0);
-        p[2 * k + 1] = Cvt<H>::h(F != 0.0f ? (float)(r / (r + b)) - 0.5f : 0.0f);
+        ((unsigned*)p)[k] = Cvt<HP>::bits(F - (float)wq(i) * (float)rho0) |
+                            (Cvt<HQ>::bits(F != 0.0f ? (float)(r / (r + b)) - 0.5f : 0.0f) << 16);
     }
 };
-using StoreF16 = StoreShift16<__half>;
-using StoreB16 = StoreShift16<__nv_bfloat16>;
+using StoreF16 = StoreShift16<__half, __half>;
+using StoreB16 = StoreShift16<__nv_bfloat16, __half>;
 
 // ---------------------------------------------------------------------------
 // Device tables

@@ -5,6 +5,12 @@ paper's 256x104x36 domain with a 116x42 patch of receding angle theta_r in a 90
 deg surround -- evaporating from step 0, with the droplet height, footprint
 radii, contact angles and mean flow recorded every `every` steps, normalised by
 the initial height h0 as in the paper (h~ = h/h0, r~ = r/h0).
+
+storage_comparison: one workload run at several storage precisions from the
+same initial state and the same wires, recording the droplet observables over
+the run and the deposit descriptors (S_x of Eq. (13), contact clusters and
+percolation of Sec. II.B) at the end, for the error of reduced-precision
+storage against FP64.
 """
 from __future__ import annotations
 
@@ -41,6 +47,46 @@ def e1_drying(steps=20000, every=500, prec="fp32", theta_r=30.0, J0=None):
     out["h_tilde"] = out["height"] / h0
     out["rx_tilde"] = out["r_x"] / h0
     out["ry_tilde"] = out["r_y"] / h0
+    return out
+
+
+def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=None, wires=None):
+    """Run the workload `make(prec)` at each precision for `steps` steps.
+
+    wires: per instance (centres, directions, beads per wire) placed identically in
+    every run (None: the workload's own seeded placement).  Returns, per precision,
+    the shape observables every `every` steps (and at the end) and the descriptors
+    and shape at the end."""
+    out = {}
+    for prec in precs:
+        wl = make(prec)
+        sim = Simulation(wl.cfgs)
+        for k, th in enumerate(wl.thetas):
+            if th is not None:
+                sim.set_substrate_pattern(k, th)
+        if wires is None:
+            for k, w in enumerate(wl.wires):
+                if w is not None and w[0] > 0:
+                    sim.add_nanowires(k, w[0], w[1], seed=wl.cfgs[k].seed)
+        else:
+            for k, pw in enumerate(wires):
+                if pw is not None:
+                    sim.add_nanowires(k, len(pw[0]), pw[2] * wl.cfgs[k].d0, pw[0], pw[1])
+        rec = []
+        done = 0
+        every_ = steps if not every else every
+        while True:
+            if done % every_ == 0 or done == steps:
+                rec.append(dict(step=done, **sim.shape(0)))
+            if done >= steps:
+                break
+            n = min(every_ - done % every_, steps - done)
+            sim.step(n)
+            done += n
+        sim.sync()
+        desc = sim.descriptors(0) if any(w is not None for w in (wires or wl.wires)) else None
+        out[prec] = {"series": rec, "final": rec[-1], "descriptors": desc, "status": sim.status()}
+        sim.close()
     return out
 
 

@@ -1,27 +1,36 @@
-"""Shifted 16-bit storage against FP64 over a drying run (the c3 comparison).
+"""Shifted 16-bit storage against FP64: the droplet and the deposit.
 
-c1 (64x32x32 cap on a 90 deg substrate, sink on from step 0) runs the same
-number of steps with FP64, FP16-shifted and BF16-shifted populations; the
-liquid volume sum (1 + C)/2 and the contact-line extents along x and y on the
-substrate (C = 0 crossings through the droplet centre, linearly interpolated)
-of the 16-bit runs are compared with the FP64 run, which the parity tests tie
-to the FP64 oracle.
+c1 (64x32x32 cap on a 90 deg substrate, sink on from step 0) runs its full
+1000 steps with FP64, FP16-shifted and BF16-shifted populations.  The liquid
+volume sum (1 + C)/2 and the contact-line extents along x and y on the
+substrate (C = 0 crossings of the first fluid layer through the droplet
+centre, linearly interpolated) of the 16-bit runs are compared with the FP64
+run, which the parity tests tie to the FP64 oracle.  The target is 1 % in
+volume and in contact-line extent for both formats.
+
+The deposit descriptors (S_x of Eq. (13); contact clusters and percolation of
+Sec. II.B) come from the 256x128x64 stripe droplet with 200 wires, run with
+identical wires in FP64, FP16 and BF16 until the droplet has dried.  The bead
+trajectories of a drying run are chaotic (contacts form or not by a fraction of
+a lattice unit), so the descriptors of the 16-bit runs are reported against
+FP64 with bounds on the statistics, not bit-level agreement.
 
 With round-to-nearest storage the sink's per-step change of the rest
 population's liquid fraction (~1e-4) is below half a unit in the last place of
-both formats and is mostly erased: after 600 steps the 16-bit runs held 2.5 %
-(FP16) and 10 % (BF16) more liquid than FP64.  The rest population is therefore
-stored with stochastic rounding; the measured drift is then -0.5 % (FP16) and
--3.2 % (BF16) in volume and 0.1 / 0.7 lattice units in contact-line extent.  The
-bounds below are those figures with about a factor two of margin.
+16-bit numbers and is mostly erased; the rest population's fraction is
+therefore stored with stochastic rounding.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
-STEPS = 600
-BOUNDS = {"fp16": dict(volume=1e-2, extent=0.3), "bf16": dict(volume=6e-2, extent=1.5)}
+STEPS_C1 = 1000
+STEPS_C2 = 10000  # the stripe droplet has dried (no liquid left) by this step
+TARGET = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +65,18 @@ def observables(sim, cfg):
     return vol, crossing_extent(C[0, yc, :]), crossing_extent(C[0, :, xc])
 
 
+def report(name, obj):
+    """Print the figures and, when REPORT_DIR is set, keep them as JSON there."""
+    print(name, json.dumps(obj))
+    d = os.environ.get("REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, f"{name}.json"), "w") as f:
+            json.dump(obj, f, indent=1)
+
+
 @pytest.fixture(scope="module")
-def runs(lbm):
+def c1_runs(lbm):
     from paper_2607_06794_b300 import workloads
 
     out = {}
@@ -65,20 +84,70 @@ def runs(lbm):
         wl = workloads.droplet_c1(prec)
         sim = lbm.Simulation(wl.cfgs)
         wl.setup(sim)
-        sim.step(STEPS)
+        sim.step(STEPS_C1)
         sim.sync()
         out[prec] = observables(sim, wl.cfgs[0])
-        print(f"c3 {prec}: volume {out[prec][0]:.6f} x-extent {out[prec][1]:.4f} y-extent {out[prec][2]:.4f}")
         assert sim.status() == 0
         sim.close()
+    rep = {p: dict(volume=v, x_extent=ex, y_extent=ey) for p, (v, ex, ey) in out.items()}
+    for p in ("fp16", "bf16"):
+        rep[p]["volume_rel_err"] = (out[p][0] - out["fp64"][0]) / out["fp64"][0]
+        rep[p]["x_extent_err"] = out[p][1] - out["fp64"][1]
+        rep[p]["y_extent_err"] = out[p][2] - out["fp64"][2]
+    report("precision_c1_1000_steps", rep)
     return out
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_low_precision_storage_tracks_fp64_over_a_drying_run(runs, prec):
-    v64, ex64, ey64 = runs["fp64"]
-    v, ex, ey = runs[prec]
+def test_16bit_storage_keeps_volume_and_contact_line_within_one_percent(c1_runs, prec):
+    v64, ex64, ey64 = c1_runs["fp64"]
+    v, ex, ey = c1_runs[prec]
     assert v64 > 1000.0 and ex64 > 20.0 and ey64 > 5.0
-    assert abs(v - v64) / v64 < BOUNDS[prec]["volume"], (prec, v, v64)
-    assert abs(ex - ex64) < BOUNDS[prec]["extent"], (prec, ex, ex64)
-    assert abs(ey - ey64) < BOUNDS[prec]["extent"], (prec, ey, ey64)
+    assert abs(v - v64) / v64 < TARGET, (prec, v, v64)
+    assert abs(ex - ex64) / ex64 < TARGET, (prec, ex, ex64)
+    assert abs(ey - ey64) / ey64 < TARGET, (prec, ey, ey64)
+
+
+@pytest.fixture(scope="module")
+def c2_deposits(lbm):
+    from paper_2607_06794_b300 import experiments, workloads
+    from tests import inputs
+
+    c = workloads.droplet_c2("fp64").cfgs[0]
+    qmax = 1.0 - np.arctanh(0.9) * c.width / min(c.a, c.b, c.c)
+    cen, dirs = inputs.wires_in_droplet(c.seed, 200, 4, c.d0, (c.nx, c.ny, c.nz), (c.cx, c.cy, c.cz),
+                                        (c.a, c.b, c.c), qmax)
+    res = experiments.storage_comparison(workloads.droplet_c2, ("fp64", "fp16", "bf16"), STEPS_C2,
+                                         every=1000, wires=[(cen, dirs, 4)])
+    rep = {}
+    for p, r in res.items():
+        d = r["descriptors"]
+        rep[p] = dict(S_x=d["S_x"], n_clusters=d["n_clusters"], percolates=d["percolates"],
+                      final_volume=r["final"]["volume"], status=r["status"],
+                      volume_series=[round(s["volume"], 2) for s in r["series"]])
+    for p in ("fp16", "bf16"):
+        rep[p]["S_x_err"] = rep[p]["S_x"] - rep["fp64"]["S_x"]
+        rep[p]["clusters_err"] = rep[p]["n_clusters"] - rep["fp64"]["n_clusters"]
+        rep[p]["percolation_agrees"] = rep[p]["percolates"] == rep["fp64"]["percolates"]
+    report("precision_c2_deposit", rep)
+    return rep
+
+
+def test_the_runs_reach_a_deposit(c2_deposits):
+    for p in ("fp64", "fp16", "bf16"):
+        r = c2_deposits[p]
+        assert r["status"] == 0, p
+        assert r["final_volume"] < 0.02 * r["volume_series"][0], p  # dried
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_deposit_descriptors_of_16bit_storage_against_fp64(c2_deposits, prec):
+    r, r64 = c2_deposits[prec], c2_deposits["fp64"]
+    # the drying time itself agrees to the 1 % volume target along the way
+    v64 = np.array(r64["volume_series"])
+    v = np.array(r["volume_series"])
+    live = v64 > 0.2 * v64[0]
+    assert np.all(np.abs(v[live] - v64[live]) <= TARGET * v64[0]), (prec, v, v64)
+    # chaotic bead trajectories: the statistics of the deposit agree
+    assert abs(r["S_x_err"]) < 0.1, r
+    assert abs(r["clusters_err"]) <= max(3, 0.25 * r64["n_clusters"]), r
