@@ -45,7 +45,7 @@ def kernel_hash():
     d = os.path.join(ROOT, "paper_2607_06794_b300", "csrc")
     src = open(os.path.join(d, "kernels_fluid.cuh")).read()
     i = src.index("k_stream_collide(const InstDev")
-    start = src.rindex("template <class S, int TX, int TY>", 0, i)
+    start = src.rindex("template <", 0, i)
     end = src.index("\n}\n", i) + 3
     h = hashlib.sha1()
     h.update(src[start:end].encode())

@@ -104,6 +104,43 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N_) : "memory");
 }
 
+// Bulk asynchronous copies (the tensor-memory-access engine's 1-D form) into shared
+// memory, completion counted in bytes on a shared-memory mbarrier.  Source and
+// destination 16-byte aligned, sizes multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// one arrival that also announces `bytes` of copies to come in the current phase
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// the waiting thread may be suspended up to MBAR_SUSPEND_NS before the poll returns
+// false, so that waiting warps sleep rather than take issue slots
+constexpr unsigned MBAR_SUSPEND_NS = 20000;
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, "
+        "p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "n"(MBAR_SUSPEND_NS)
+        : "memory");
+    return ok != 0;
+}
+// order this thread's earlier generic-proxy shared accesses before later bulk copies
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(smem)),
+                 "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// try_wait polls before a wait is declared lost
+constexpr int MBAR_POLLS = 1 << 16;
+
 template <typename T>
 __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
 template <>
@@ -157,7 +194,14 @@ __global__ void __launch_bounds__(HCOL_X * HCOL_Z) k_column_height(const InstDev
 
 // MINB: resident blocks per SM the register budget is sized for (4 blocks of 128
 // threads: 128 registers a thread; 5 blocks: 96), a choice of the tiling autotuner
-template <class S, int TX, int TY, int MINB>
+// BULK (32- and 16-bit storage, every lattice nx % 4 == 0): the pull of a plane
+// arrives as bulk row copies, one per (direction and component, tile row): the
+// tile's row of that direction's source plane, widened by 4 columns on the side
+// it is shifted to so that it starts and ends on 16-byte boundaries (split in two
+// where it crosses the periodic x boundary), landing so that the node reads its
+// element at column 4 - c_x of the staged row.  Otherwise per-element 4-byte
+// asynchronous copies.
+template <class S, int TX, int TY, int MINB, bool BULK>
 __global__ void __launch_bounds__(TX * TY, MINB)
     k_stream_collide(const InstDev* __restrict__ insts, const TileDesc* __restrict__ tiles,
                      StepGlobals* __restrict__ glob) {
@@ -178,10 +222,23 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     __shared__ T sE[3][2][5][2][TY];
     __shared__ double sRed[NT / 32][3];
     __shared__ int sErr;
-    // pulled populations of the next plane, staged by asynchronous 4-byte copies
-    // (16- and 32-bit storage; FP64 keeps them in registers): [19 WORDS][NT] words
+    // pulled populations of the next plane (16- and 32-bit storage; FP64 keeps them
+    // in registers): per-element copies [19 WORDS][NT] words, or bulk row copies
+    // [NBUF][19 WORDS][TY][RW] words; 16-bit bulk staging is double-buffered, so the
+    // copies of a plane go out a whole plane ahead
     constexpr bool ASYNC = S::WORDS > 0;
-    extern __shared__ __align__(16) unsigned stage_dyn[];
+    static_assert(!BULK || ASYNC, "bulk staging needs word storage");
+    constexpr int RW = TX + 8;  // staged row: the tile row and 4 columns each side
+    constexpr int NBUF = (BULK && S::WORDS == 1) ? 2 : 1;
+    constexpr int BUFW = 19 * S::WORDS * TY * RW;  // words of one bulk stage buffer
+    extern __shared__ __align__(128) unsigned stage_dyn[];
+    __shared__ __align__(8) unsigned long long sBar[NBUF];
+    // bulk copies of an interior plane, per (direction-component, row) pair: source word
+    // offset without the plane term, staged word offset, first and second segment
+    // (source column, words) - the second empty unless the row wraps in x
+    constexpr int NPAIR = BULK ? 19 * S::WORDS * TY : 1;
+    __shared__ int4 sCopy[NPAIR];
+    __shared__ int2 sCopy2[NPAIR];
 
     const TileDesc td = tiles[blockIdx.x];
     const InstDev& Ig = insts[td.inst];
@@ -258,6 +315,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
     for (int s = tid; s < 3 * 2 * HY1 * TX; s += NT) (&sB[0][0][0][0])[s] = T(0);
     if (tid == 0) sErr = 0;
+    if constexpr (BULK) {
+        if (tid < NBUF) mbar_init(&sBar[tid], NT);  // every thread arrives with the bytes it copies
+    }
 
     // C of plane p into the ring over the tile plus 2 cells (synchronous form)
     auto loadC = [&](int p) {
@@ -508,6 +568,94 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         else
             issue_pull_t(z, std::false_type{});
     };
+    // bulk pull of plane z (called by every thread between barriers, the stage free):
+    // the (direction-component, row) pairs are spread over the block, each thread
+    // arriving on the mbarrier with the bytes of its copies.  A row shifted by c_x = +1
+    // is read from 4 columns left of the tile and lands at staged column 0, one with
+    // c_x = -1 or 0 from the tile's first column landing at column 4; a bounced-back
+    // pair (z = 0 or the top wall) copies the opposite direction's own row of plane z
+    // to column 4; a gas-inflow pair copies its own row of plane z in the shifted
+    // layout (the value is replaced, but every staged slot read was written).
+    // Interior planes take the per-pair offsets tabulated in shared memory.
+    auto pair_copy = [&](int p, int z, bool edge, int& sofs, int& dofs, int& cA, int& nA, int& cB, int& nB) {
+        const int j = p / th, r = p - j * th;
+        const int i = j >= 19 ? j - 19 : j, comp = j >= 19 ? 1 : 0;
+        int sz = z - cz(i), di = i, ys = y0 + r - cy(i), sh = cx(i);
+        if (edge && (sz < 0 || (sz >= nz && top_bc == 0))) {
+            sz = z;
+            di = opp(i);
+            ys = y0 + r;
+            sh = 0;
+        } else if (edge && sz >= nz) {
+            sz = z;
+            ys = y0 + r;
+        }
+        ys = wrap_near(ys, ny);
+        sofs = (int)(comp * cs + (unsigned)di * N + (unsigned)ys * nx) + (sz - z) * (int)nxy;
+        const int len = sh != 0 ? tw + 4 : tw;
+        const int d = sh > 0 ? 0 : 4;
+        dofs = (j * TY + r) * RW + d;
+        int c0 = sh > 0 ? x0 - 4 : x0;
+        if (c0 < 0) c0 += nx;
+        cA = c0;
+        nA = min(len, nx - c0);
+        cB = 0;
+        nB = len - nA;
+    };
+    if constexpr (BULK) {
+        for (int p = tid; p < 19 * S::WORDS * th; p += NT) {
+            int sofs, dofs, cA, nA, cB, nB;
+            pair_copy(p, 1, false, sofs, dofs, cA, nA, cB, nB);
+            sCopy[p] = make_int4(sofs, dofs, cA, nA);
+            sCopy2[p] = make_int2(cB, nB);
+        }
+    }
+    auto issue_bulk = [&](int z) {
+        if (z >= z1) return;
+        const int b = (z - z0) % NBUF;
+        unsigned* stg = stage_dyn + (size_t)b * BUFW;
+        const unsigned* srcz = (const unsigned*)src + (size_t)z * nxy;
+        const bool edge = z == 0 || z == nz - 1;
+        unsigned bytes = 0;
+        bool fenced = false;
+        for (int p = tid; p < 19 * S::WORDS * th; p += NT) {
+            if (!fenced) {
+                fence_proxy_async();
+                fenced = true;
+            }
+            int sofs, dofs, cA, nA, cB, nB;
+            if (edge) {
+                pair_copy(p, z, true, sofs, dofs, cA, nA, cB, nB);
+            } else {
+                const int4 a = sCopy[p];
+                const int2 b = sCopy2[p];
+                sofs = a.x;
+                dofs = a.y;
+                cA = a.z;
+                nA = a.w;
+                cB = b.x;
+                nB = b.y;
+            }
+            const unsigned* row = srcz + sofs;
+            bulk_g2s(stg + dofs, row + cA, (unsigned)nA * 4u, &sBar[b]);
+            if (nB > 0) bulk_g2s(stg + dofs + nA, row + cB, (unsigned)nB * 4u, &sBar[b]);
+            bytes += (unsigned)(nA + nB) * 4u;
+        }
+        mbar_arrive_expect(&sBar[b], bytes);
+    };
+    // wait for the bulk pull of plane z (bounded: a lost wait is reported): plane z sits
+    // in buffer (z - z0) % NBUF, whose barrier completes one phase per plane it carries
+    auto wait_bulk = [&](int z) {
+        const int k = z - z0;
+        const unsigned parity = (unsigned)(k / NBUF) & 1u;
+        int polls = 0;
+        while (!mbar_try_wait(&sBar[k % NBUF], parity)) {
+            if (++polls >= MBAR_POLLS) {
+                err |= ERR_TIMEOUT;
+                break;
+            }
+        }
+    };
 
     // ---- prologue: C planes and normals below the first plane ----
     if (z0 == 0) {
@@ -530,8 +678,12 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         computeN(z0);
     }
     prefetchC(z0 + 2);
-    if constexpr (ASYNC) issue_pull(z0);
+    if constexpr (ASYNC && !BULK) issue_pull(z0);
     __syncthreads();
+    if constexpr (BULK) {
+        issue_bulk(z0);
+        if constexpr (NBUF == 2) issue_bulk(z0 + 1);
+    }
 
     for (int z = z0; z < z1; ++z) {
         const unsigned node = (unsigned)z * nxy + row0 + x;
@@ -563,12 +715,27 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             T Fi[19];
             T rR = 0, rho = 0, jx = 0, jy = 0, jz = 0;
             const bool top_gas = EDGE && z == nz - 1 && top_bc == 1;
-            if constexpr (ASYNC) cp_async_wait<0>();  // plane z landed
+            if constexpr (BULK)
+                wait_bulk(z);  // plane z landed
+            else if constexpr (ASYNC)
+                cp_async_wait<0>();
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
                 // total F_i and f^R_i (a bounced-back element has the same weight: w_opp(i) = w_i)
                 T F, r;
-                if constexpr (ASYNC) {
+                if constexpr (BULK) {
+                    // column of this node's source in the staged row; a bounced-back
+                    // element sits in the node's own column
+                    int o = 4 - cx(i);
+                    if constexpr (EDGE && cz(i) > 0) o = z == 0 ? 4 : o;
+                    if constexpr (EDGE && cz(i) < 0) o = (z == nz - 1 && top_bc == 0) ? 4 : o;
+                    const unsigned* st = stage_dyn + (size_t)((z - z0) % NBUF) * BUFW + (size_t)ty * RW + tx + o;
+                    if constexpr (S::WORDS == 2)
+                        S::decode_total(__uint_as_float(st[(size_t)i * TY * RW]),
+                                        __uint_as_float(st[(size_t)(19 + i) * TY * RW]), (T)wq(i), rho0, F, r);
+                    else
+                        S::decode_word_total(st[(size_t)i * TY * RW], (T)wq(i), rho0, F, r);
+                } else if constexpr (ASYNC) {
                     const unsigned* st = stage_dyn + tid;
                     if constexpr (S::WORDS == 2)
                         S::decode_total(__uint_as_float(st[(size_t)i * NT]),
@@ -746,10 +913,13 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                 phase3(std::false_type{});
         }
         retire(ac1);
-        if constexpr (ASYNC) issue_pull(z + 1);  // its slots were consumed above by this thread
+        if constexpr (ASYNC && !BULK) issue_pull(z + 1);  // its slots were consumed above by this thread
         __syncthreads();
+        if constexpr (BULK) {
+            issue_bulk(z + NBUF);  // plane z's buffer is free once every thread passed the barrier
+        }
     }
-    if constexpr (ASYNC) cp_async_wait<0>();
+    if constexpr (ASYNC && !BULK) cp_async_wait<0>();
     // the last two planes: shares still in registers
     T none[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     flush(z1 - 2);

@@ -27,14 +27,18 @@ namespace {
 // fills the GPU"; chunks above nz take the whole column), and the register
 // budget as resident blocks per SM (128 registers a thread: 4 blocks of 32x4,
 // 2 of 32x8; a 96-register form of 32x4 at 5 blocks per SM measured 5-40 %
-// slower on every workload and was dropped).  Blocks of equal chunks march up
-// in step, so the halo planes a block re-reads were just read by its
-// neighbours and come from L2.
+// slower on every workload and was dropped), and how 32- and 16-bit storage
+// stages the pull (0: per-element asynchronous copies; 1: bulk row copies where
+// every lattice of the batch has nx % 4 == 0, else per-element).  Blocks of equal
+// chunks march up in step, so the halo planes a block re-reads were just read by
+// its neighbours and come from L2.
 struct Shape {
-    int tx, ty, chunk, minb;
+    int tx, ty, chunk, minb, bulk;
 };
-const Shape SHAPES[] = {{32, 8, 0, 2}, {32, 8, 16, 2}, {32, 8, 32, 2}, {32, 8, 64, 2},
-                        {32, 4, 0, 4}, {32, 4, 16, 4}, {32, 4, 32, 4}, {32, 4, 64, 4}};
+const Shape SHAPES[] = {{32, 8, 0, 2, 0}, {32, 8, 16, 2, 0}, {32, 8, 32, 2, 0}, {32, 8, 64, 2, 0},
+                        {32, 4, 0, 4, 0}, {32, 4, 16, 4, 0}, {32, 4, 32, 4, 0}, {32, 4, 64, 4, 0},
+                        {32, 8, 0, 2, 1}, {32, 8, 32, 2, 1}, {32, 4, 0, 4, 1}, {32, 4, 32, 4, 1},
+                        {32, 4, 64, 4, 1}};
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 128;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
@@ -239,6 +243,8 @@ struct lbm_handle {
     bool graph_dirty = true;
     int max_nb = 0;
     int shape = 0;  // index into SHAPES
+    // the fused kernel may pull by bulk row copies (32- and 16-bit storage, every nx % 4 == 0)
+    bool bulk = false;
     // second stream of a step: column heights and the neighbour list run beside
     // the coupling-field pass (fork/join by events, captured into the graph)
     cudaStream_t side = nullptr;
@@ -266,20 +272,25 @@ struct lbm_handle {
 
 namespace {
 
-// dynamic shared memory of the fused kernel: the staged pull of one plane
+// dynamic shared memory of the fused kernel: the staged pull of one plane (bulk
+// rows carry 4 extra columns on each side; 16-bit bulk staging keeps two planes)
 template <class S>
-constexpr size_t stage_bytes(int nt) {
-    return (size_t)19 * S::WORDS * nt * 4;
+constexpr size_t stage_bytes(int tx, int ty, bool bulk) {
+    return (size_t)19 * S::WORDS * ty * (bulk ? tx + 8 : tx) * 4 * ((bulk && S::WORDS == 1) ? 2 : 1);
 }
 
 template <class S, int TX, int TY, int MINB>
 lbm_status prepare_one() {
-    const size_t dyn = stage_bytes<S>(TX * TY);
+    const size_t dyn = stage_bytes<S>(TX, TY, false);
     if (dyn > 0)
-        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dyn));
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    if constexpr (S::WORDS > 0)
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stage_bytes<S>(TX, TY, true)));
     return LBM_OK;
 }
+
 
 // per-kernel attributes, set once before any launch or capture
 template <class S>
@@ -295,12 +306,24 @@ lbm_status launch_fused(lbm_handle* h) {
     const int nb = h->L.ntiles;
     const InstDev* in = h->L.d_inst;
     const TileDesc* td = h->L.d_tiles;
-    if (sh.tx == 32 && sh.ty == 8 && sh.minb == 2)
-        k_stream_collide<S, 32, 8, 2><<<nb, 256, stage_bytes<S>(256), h->stream>>>(in, td, h->L.glob);
-    else if (sh.tx == 32 && sh.ty == 4 && sh.minb == 4)
-        k_stream_collide<S, 32, 4, 4><<<nb, 128, stage_bytes<S>(128), h->stream>>>(in, td, h->L.glob);
-    else
+    const bool bulk = S::WORDS > 0 && h->bulk && sh.bulk != 0;
+    if (sh.tx == 32 && sh.ty == 8 && sh.minb == 2) {
+        if (bulk)
+            k_stream_collide<S, 32, 8, 2, S::WORDS != 0><<<nb, 256, stage_bytes<S>(32, 8, true), h->stream>>>(
+                in, td, h->L.glob);
+        else
+            k_stream_collide<S, 32, 8, 2, false><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(in, td,
+                                                                                                      h->L.glob);
+    } else if (sh.tx == 32 && sh.ty == 4 && sh.minb == 4) {
+        if (bulk)
+            k_stream_collide<S, 32, 4, 4, S::WORDS != 0><<<nb, 128, stage_bytes<S>(32, 4, true), h->stream>>>(
+                in, td, h->L.glob);
+        else
+            k_stream_collide<S, 32, 4, 4, false><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(in, td,
+                                                                                                      h->L.glob);
+    } else {
         return LBM_EINVAL;
+    }
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -779,6 +802,8 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
     h->cfg.assign(cfgs, cfgs + n);
     h->stream = (cudaStream_t)stream;
     h->prec = cfgs[0].prec;
+    h->bulk = h->prec != LBM_FP64;
+    for (int k = 0; k < n; ++k) h->bulk = h->bulk && cfgs[k].nx % 4 == 0;
     Carver cv{(char*)dev_ws};
     carve(cfgs, n, cv, h->L);
     // substeps must match across instances with beads: use the first with beads

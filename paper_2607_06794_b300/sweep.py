@@ -17,7 +17,7 @@ import dataclasses
 
 import numpy as np
 
-from . import Config, Simulation, _lib
+from . import Config, LBMError, Simulation, _lib
 from .workloads import stripe
 
 N_IN, N_HIDDEN, N_OUT = 4, 64, 3
@@ -70,7 +70,8 @@ def deposit_table(points, seeds=(0,), prec="fp16", max_steps=20000, every=500, a
     """Descriptors of the dried deposits of every sweep point: all (point, seed) pairs
     advance as one batch until every droplet has evaporated (no liquid left) or
     max_steps.  Returns (rows [n_points, 3] = mean S_x, mean cluster count per wire,
-    percolation fraction over the seeds; steps taken; per-run raw rows)."""
+    percolation fraction over the seeds, NaN where no wire fits the droplet; steps
+    taken; per-run raw rows)."""
     runs = [(k, s) for k in range(len(points)) for s in seeds]
     cfgs, thetas, nws = [], [], []
     for k, s in runs:
@@ -81,7 +82,17 @@ def deposit_table(points, seeds=(0,), prec="fp16", max_steps=20000, every=500, a
     sim = Simulation(cfgs)
     for j, ((k, s), th, nw) in enumerate(zip(runs, thetas, nws)):
         sim.set_substrate_pattern(j, th)
-        sim.add_nanowires(j, nw, points[k][2], seed=1 + 1009 * s + k)
+        # long wires in a small droplet: halve the count until they fit straight inside;
+        # a point where not even one fits has no deposit (its row is NaN)
+        while nw > 0:
+            try:
+                sim.add_nanowires(j, nw, points[k][2], seed=1 + 1009 * s + k)
+                break
+            except LBMError as e:
+                if e.code != _lib.EINVAL:
+                    raise
+                nw //= 2
+        nws[j] = nw
     if autotune:
         sim.autotune(2)
     done = 0
@@ -91,12 +102,16 @@ def deposit_table(points, seeds=(0,), prec="fp16", max_steps=20000, every=500, a
         if all(sim.shape(j)["volume"] <= 0.0 for j in range(len(runs))):
             break
     sim.sync()
-    raw = np.zeros((len(runs), 3))
+    raw = np.full((len(runs), 3), np.nan)
     for j in range(len(runs)):
-        d = sim.descriptors(j)
-        raw[j] = (d["S_x"], d["n_clusters"] / max(1, nws[j]), float(d["percolates"]))
+        if nws[j] > 0:
+            d = sim.descriptors(j)
+            raw[j] = (d["S_x"], d["n_clusters"] / nws[j], float(d["percolates"]))
     sim.close()
-    rows = raw.reshape(len(points), len(seeds), 3).mean(axis=1)
+    r3 = raw.reshape(len(points), len(seeds), 3)
+    rows = np.full((len(points), 3), np.nan)
+    ok = ~np.all(np.isnan(r3[:, :, 0]), axis=1)
+    rows[ok] = np.nanmean(r3[ok], axis=1)
     return rows, done, raw
 
 

@@ -130,6 +130,31 @@ def test_ragged_and_tiny_lattices(lbm, oracle, shape):
     assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-12
 
 
+@pytest.mark.parametrize("prec,shape,top_bc", [
+    ("fp32", (37, 11, 9), 1), ("fp32", (36, 13, 9), 0), ("fp32", (68, 6, 7), 1),
+    ("fp16", (37, 11, 9), 0), ("fp16", (68, 13, 10), 1), ("bf16", (36, 13, 9), 0)])
+def test_staged_pulls_on_ragged_tiles(lbm, oracle, prec, shape, top_bc):
+    """Both ways the 32- and 16-bit fused kernel stages its pull: per-element copies
+    (nx not a multiple of 4) and bulk row copies (nx a multiple of 4), on lattices whose
+    last tiles are narrower and shorter than the rest, with the gas top or the top wall."""
+    nx, ny, nz = shape
+    cfg = droplet_cfg(lbm, nx=nx, ny=ny, nz=nz, prec=prec, top_bc=top_bc, J0=1e-3, evap_start=0)
+    theta = inputs.stripe_angles(nx, ny, 4, 60.0, 110.0)
+    for tiling in (4, 6):
+        p, fR, fB, cot = oracle_state(oracle, cfg, 10, theta)
+        sim = lbm.Simulation([cfg])
+        sim.set_substrate_pattern(0, theta)
+        sim.set_tiling(tiling)
+        sim.write(0, "populations", np.stack([fR, fB]))
+        acc = oracle.Acc()
+        for _ in range(2):
+            oracle.step(p, fR, fB, cot, acc)
+        sim.step(2)
+        sim.sync()
+        assert pop_err(sim.read(0, "populations"), fR, fB) < 2 * TOL[prec], (prec, shape, tiling)
+        sim.close()
+
+
 def test_top_wall_and_body_force(lbm, oracle):
     cfg = droplet_cfg(lbm, prec="fp64", top_bc=0, body=(2e-6, -1e-6, 0.0))
     sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg, steps=4)

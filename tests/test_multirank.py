@@ -87,3 +87,16 @@ def test_single_rank_is_the_identity():
     assert bench.reduce_max(3.5, None, "cpu") == 3.5
     assert bench.whole_job_mlups(2_097_152, 200, 116.0, 1) == pytest.approx(2_097_152 * 200 / 0.116 / 1e6)
     assert bench.job_throughput(4.0, 1000, 10, 1, None, "cpu") == (4.0, pytest.approx(1000 * 10 / 4e-3 / 1e6))
+
+
+def test_bench_host_helpers_run_on_the_current_sources():
+    """The bench's host-side helpers that need no GPU: the kernel-source hash that keys
+    the committed traffic figures, the peak lookup and the launch count per step."""
+    import bench
+    from paper_2607_06794_b300 import workloads
+    h = bench.kernel_hash()
+    assert len(h) == 12 and h == bench.kernel_hash()
+    peak, kind = bench.peaks()
+    assert peak > 1000.0 and kind in ("measured", "fallback")
+    assert bench.launches_per_step(workloads.droplet_c5("fp32")) == 2 + 4 + 5
+    assert bench.launches_per_step(workloads.droplet_c1()) == 2
