@@ -94,6 +94,10 @@ typedef struct lbm_config {
     double rcon;           /* contact cut-off of the network model (paper: 2.1) */
     double x_src, x_snk;   /* electrodes: beads with x < x_src / x > x_snk */
     uint64_t seed;         /* seed of lbm_add_nanowires' random placement */
+    int inplace;           /* population storage: 0 two buffers (read one, write the other);
+                              1 esoteric pull, one buffer read and written in place plus wall
+                              ghost slots (half the population memory, same bytes moved per
+                              step); equal across a batch */
 } lbm_config;
 
 typedef struct lbm_descriptors {

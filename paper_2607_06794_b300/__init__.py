@@ -85,6 +85,7 @@ class Config:
     x_src: float = -math.inf
     x_snk: float = math.inf
     seed: int = 1234
+    inplace: int = 0  # 1: esoteric-pull in-place population storage
 
     def to_c(self) -> _lib.lbm_config:
         c = _lib.lbm_config()

@@ -37,6 +37,7 @@ class lbm_config(C.Structure):
         ("gamma", C.c_double), ("xi", C.c_double), ("mu", C.c_double), ("gamma_t", C.c_double),
         ("bead_mass", C.c_double), ("substeps", C.c_int), ("max_beads", C.c_int),
         ("rcon", C.c_double), ("x_src", C.c_double), ("x_snk", C.c_double), ("seed", C.c_uint64),
+        ("inplace", C.c_int),
     ]
 
 

@@ -215,9 +215,7 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     __shared__ T sN[10][10][10][3];
     const long long step = __ldcg(&glob->step);
     const T* rho = (const T*)I.rho[step % 3];
-    const E* src = (const E*)I.pop[step & 1];
     const int nx = I.nx, ny = I.ny, nz = I.nz;
-    const long long N = I.N, cs = 19 * N;
     const int X0 = (t % I.t8x) * 8, Y0 = ((t / I.t8x) % I.t8y) * 8, Z0 = (t / (I.t8x * I.t8y)) * 8;
     const int tid = threadIdx.x;
     __syncthreads();  // shared blocks of the previous tile are free
@@ -230,7 +228,7 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
         T c = T(0);
         if (z >= 0 && z <= nz) {
             const int x = wrap_near(X0 - 2 + lx, nx), y = wrap_near(Y0 - 2 + ly, ny);
-            c = colour_of(rho, N, ((long long)(z < nz ? z : nz - 1) * ny + y) * nx + x);
+            c = colour_of(rho, I.N, ((long long)(z < nz ? z : nz - 1) * ny + y) * nx + x);
         }
         sC[lz][ly][lx] = c;
     }
@@ -330,22 +328,10 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     const T hs = T(0.5) * (T)I.sigma;
     const T rho0 = (T)I.rho0;
     T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
-    const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx), ym = wrap1(y - 1, ny), yp = wrap1(y + 1, ny);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const int sz = z - cz(i);
         T r, b;
-        if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
-            S::load(src, cs, (long long)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
-        } else if (sz >= nz) {
-            r = T(0);
-            b = (T)wq(i) * rho0;
-        } else {
-            const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
-            const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
-            S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i), rho0,
-                    r, b);
-        }
+        pull_streamed<S>(I, step, i, x, y, z, r, b);
         rR += r;
         rB += b;
         const T F = r + b;

@@ -201,7 +201,9 @@ __global__ void __launch_bounds__(HCOL_X * HCOL_Z) k_column_height(const InstDev
 // where it crosses the periodic x boundary), landing so that the node reads its
 // element at column 4 - c_x of the staged row.  Otherwise per-element 4-byte
 // asynchronous copies.
-template <class S, int TX, int TY, int MINB, bool BULK>
+// EP: esoteric-pull in-place storage (one buffer and the wall ghost slots; the
+// slot rules are ep_load / ep_store / ep_outflow); per-element or register pulls.
+template <class S, int TX, int TY, int MINB, bool BULK, bool EP>
 __global__ void __launch_bounds__(TX * TY, MINB)
     k_stream_collide(const InstDev* __restrict__ insts, const TileDesc* __restrict__ tiles,
                      StepGlobals* __restrict__ glob) {
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     // copies of a plane go out a whole plane ahead
     constexpr bool ASYNC = S::WORDS > 0;
     static_assert(!BULK || ASYNC, "bulk staging needs word storage");
+    static_assert(!(BULK && EP), "in-place storage pulls element by element");
     constexpr int RW = TX + 8;  // staged row: the tile row and 4 columns each side
     constexpr int NBUF = (BULK && S::WORDS == 1) ? 2 : 1;
     constexpr int BUFW = 19 * S::WORDS * TY * RW;  // words of one bulk stage buffer
@@ -249,8 +252,14 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const long long step = __ldcg(&glob->step);
     const int pa = (int)(step & 1);
     const int pr = (int)(step % 3);
+    // two buffers: read one, write the other.  In place both name the one buffer: each
+    // slot is read and written by one node of the step, its pull loads (phase 1 or the
+    // previous plane) are separated from its stores (phase 3) by block barriers, and the
+    // outflow read of phase 3 touches a slot that no store of that node writes
     const E* __restrict__ src = (const E*)Ig.pop[pa];
     E* __restrict__ dst = (E*)Ig.pop[pa ^ 1];
+    E* gslot = (E*)Ig.ghost;  // in place: the wall ghost slots
+    const unsigned gcs = 10u * nxy;  // component stride of the ghost slots
     const T* __restrict__ rho_r = (const T*)Ig.rho[pr];
     T* __restrict__ rho_w = (T*)Ig.rho[(pr + 1) % 3];
     T* __restrict__ rho_z = (T*)Ig.rho[(pr + 2) % 3];
@@ -531,6 +540,24 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const unsigned rowm = (unsigned)ym * nx, row0 = (unsigned)y * nx, rowp = (unsigned)yp * nx;
 
+    // in place: where direction i of this thread's node of plane z is read (interior
+    // planes: no ghost slot, no gas inflow)
+    auto pull_ep = [&](int z, auto I_, auto EDGE_) -> PopLoc {
+        constexpr int i = decltype(I_)::value;
+        if constexpr (decltype(EDGE_)::value) {
+            PopLoc L;
+            ep_load(i, x, y, z, pa, nx, ny, nz, top_bc, L);
+            return L;
+        } else {
+            const unsigned node = (unsigned)z * nxy + row0 + x;
+            if constexpr (i == 0) return {node, false};
+            if constexpr (i & 1) return {(pa ? (unsigned)i : (unsigned)(i + 1)) * N + node, false};
+            // the even member comes from n + c_{i-1}, the two-buffer source node
+            const int sx = cx(i) == 1 ? xm : (cx(i) == -1 ? xp : x);
+            const unsigned row = cy(i) == 1 ? rowm : (cy(i) == -1 ? rowp : row0);
+            return {(pa ? (unsigned)i : (unsigned)(i - 1)) * N + (unsigned)(z - cz(i)) * nxy + row + sx, false};
+        }
+    };
     // element of direction i that streams into this thread's node of plane z; EDGE:
     // z may be the bottom or the top plane (interior planes need no boundary test)
     auto pull_index = [&](int z, int i, auto EDGE_) -> unsigned {
@@ -551,12 +578,24 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             unsigned* st = stage_dyn + tid;
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                const unsigned k = pull_index(z, i, EDGE_);
-                if constexpr (S::WORDS == 2) {
-                    cp_async4(st + (size_t)i * NT, src + k);
-                    cp_async4(st + (size_t)(19 + i) * NT, src + cs + k);
+                const E* base = src;
+                unsigned k, kc = cs;
+                (void)kc;
+                if constexpr (EP) {
+                    const PopLoc L = pull_ep(z, I_, EDGE_);
+                    k = L.k;
+                    if (L.ghost) {
+                        base = gslot;
+                        kc = gcs;
+                    }
                 } else {
-                    cp_async4(st + (size_t)i * NT, (const unsigned*)src + k);
+                    k = pull_index(z, i, EDGE_);
+                }
+                if constexpr (S::WORDS == 2) {
+                    cp_async4(st + (size_t)i * NT, base + k);
+                    cp_async4(st + (size_t)(19 + i) * NT, base + kc + k);
+                } else {
+                    cp_async4(st + (size_t)i * NT, (const unsigned*)base + k);
                 }
             });
         }
@@ -695,9 +734,17 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         } else if (active) {
             static_for<0, 19>([&](auto I_) {
                 constexpr int i = decltype(I_)::value;
-                const unsigned k = pull_index(z, i, std::true_type{});
-                rawR[i] = __ldg(src + k);
-                rawB[i] = __ldg(src + cs + k);
+                if constexpr (EP) {
+                    const PopLoc L = pull_ep(z, I_, std::true_type{});
+                    const E* base = L.ghost ? gslot : src;
+                    const unsigned kc = L.ghost ? gcs : cs;
+                    rawR[i] = base[L.k];
+                    rawB[i] = base[kc + L.k];
+                } else {
+                    const unsigned k = pull_index(z, i, std::true_type{});
+                    rawR[i] = __ldg(src + k);
+                    rawB[i] = __ldg(src + cs + k);
+                }
             });
         }
         flush(z - 2);
@@ -763,7 +810,12 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                     constexpr int i = decltype(I_)::value;
                     if constexpr (cz(i) > 0) {
                         T r, b;
-                        S::load(src, cs, (unsigned)i * N + node, (T)wq(i), rho0, r, b);
+                        if constexpr (EP) {
+                            const PopLoc L = ep_outflow(i, x, y, pa, nx, ny, nz);
+                            S::load(L.ghost ? gslot : src, L.ghost ? gcs : cs, L.k, (T)wq(i), rho0, r, b);
+                        } else {
+                            S::load(src, cs, (unsigned)i * N + node, (T)wq(i), rho0, r, b);
+                        }
                         top_out += r + b;
                     }
                 });
@@ -832,10 +884,28 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                     evap_sum += d;
                 }
                 T rq, bq;
-                if constexpr (i == 0)  // the sink's population: stochastic rounding in 16-bit storage
+                if constexpr (i == 0) {  // the sink's population: stochastic rounding in 16-bit storage
                     S::store_sr(dst, cs, node, w, rho0, r, b, rq, bq, hash32(node ^ step_key));
-                else
+                } else if constexpr (EP) {
+                    // in place: the odd member goes to its destination n + c_i (a ghost slot
+                    // beyond a wall or the gas top), the even member stays at its node
+                    if constexpr (i & 1) {
+                        if (EDGE && (z + cz(i) < 0 || z + cz(i) >= nz)) {
+                            const PopLoc L = ep_store(i, x, y, z, pa, nx, ny, nz);
+                            S::store(gslot, gcs, L.k, w, rho0, r, b, rq, bq);
+                        } else {
+                            const int tx_ = cx(i) == 1 ? xp : (cx(i) == -1 ? xm : x);
+                            const unsigned trow = cy(i) == 1 ? rowp : (cy(i) == -1 ? rowm : row0);
+                            S::store(dst, cs,
+                                     (pa ? (unsigned)(i + 1) : (unsigned)i) * N + (unsigned)(z + cz(i)) * nxy + trow + tx_,
+                                     w, rho0, r, b, rq, bq);
+                        }
+                    } else {
+                        S::store(dst, cs, (pa ? (unsigned)(i - 1) : (unsigned)i) * N + node, w, rho0, r, b, rq, bq);
+                    }
+                } else {
                     S::store(dst, cs, (unsigned)i * N + node, w, rho0, r, b, rq, bq);
+                }
                 const int tz = z + cz(i);  // the same for the whole block
                 if (EDGE && (tz < 0 || (tz >= nz && top_bc == 0))) {
                     ac0[1][0] += rq;  // bounces back to this node
@@ -964,32 +1034,74 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 // and after populations are written from the host.  Writes rho[pr] (both
 // components) and clears the next buffer.
 // ---------------------------------------------------------------------------
+// The streamed population i of node (x, y, z) at `step` in the compute type, under
+// either storage layout (two buffers: pulled from x - c_i of the buffer of the step's
+// parity, bounced back at the walls, gas equilibrium from above the gas top).
+template <class S>
+__device__ __forceinline__ void pull_streamed(const InstDev& I, long long step, int i, int x, int y, int z,
+                                              typename S::T& r, typename S::T& b) {
+    using T = typename S::T;
+    using E = typename S::E;
+    const T rho0 = (T)I.rho0;
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    if (I.inplace) {
+        PopLoc L;
+        if (!ep_load(i, x, y, z, (int)(step & 1), nx, ny, nz, I.top_bc, L)) {
+            r = T(0);
+            b = (T)wq(i) * rho0;
+            return;
+        }
+        const E* base = L.ghost ? (const E*)I.ghost : (const E*)I.pop[0];
+        S::load(base, L.ghost ? 10u * (unsigned)nx * ny : 19u * (unsigned)I.N, L.k, (T)wq(i), rho0, r, b);
+        return;
+    }
+    const long long N = I.N;
+    const E* src = (const E*)I.pop[step & 1];
+    const unsigned cs = 19u * (unsigned)N;
+    const long long node = ((long long)z * ny + y) * nx + x;
+    const int sz = z - cz(i);
+    if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
+        S::load(src, cs, (unsigned)((long long)opp(i) * N + node), (T)wq(opp(i)), rho0, r, b);
+    } else if (sz >= nz) {
+        r = T(0);
+        b = (T)wq(i) * rho0;
+    } else {
+        const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
+        S::load(src, cs, (unsigned)((long long)i * N + ((long long)sz * ny + sy) * nx + sx), (T)wq(i), rho0, r, b);
+    }
+}
+
+// Where the post-collision population i of node n, as left by the step before
+// `step`, is stored: base pointer, component stride and element index.
+template <class S>
+__device__ __forceinline__ void post_place(const InstDev& I, long long step, int i, long long n,
+                                           typename S::E*& base, long long& cs, long long& k) {
+    using E = typename S::E;
+    if (I.inplace) {
+        const int nx = I.nx, ny = I.ny;
+        const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+        const PopLoc L = ep_store(i, x, y, z, (int)((step - 1) & 1), nx, ny, I.nz);
+        base = L.ghost ? (E*)I.ghost : (E*)I.pop[0];
+        cs = L.ghost ? 10LL * nx * ny : 19 * I.N;
+        k = L.k;
+        return;
+    }
+    base = (E*)I.pop[step & 1];
+    cs = 19 * I.N;
+    k = (long long)i * I.N + n;
+}
+
 // rho_R, rho_B, j of node n from the populations that stream into it at `step`
 template <class S>
 __device__ void stream_moments(const InstDev& I, long long step, long long n, typename S::T* m) {
     using T = typename S::T;
-    using E = typename S::E;
-    const long long N = I.N;
-    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const int nx = I.nx, ny = I.ny;
     const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
-    const E* src = (const E*)I.pop[step & 1];
-    const long long cs = 19 * N;
-    const T rho0 = (T)I.rho0;
     T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const int sz = z - cz(i);
         T r, b;
-        if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
-            S::load(src, cs, (long long)opp(i) * N + n, (T)wq(opp(i)), rho0, r, b);
-        } else if (sz >= nz) {
-            r = T(0);
-            b = (T)wq(i) * rho0;
-        } else {
-            const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
-            S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i),
-                    rho0, r, b);
-        }
+        pull_streamed<S>(I, step, i, x, y, z, r, b);
         rR += r;
         rB += b;
         const T F = r + b;
@@ -1008,38 +1120,13 @@ template <class S>
 __global__ void k_moments(InstDev I, long long step, long long n0, long long len,
                           double* __restrict__ diag) {
     using T = typename S::T;
-    using E = typename S::E;
     const long long N = I.N;
     const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (u >= len) return;
     const long long n = n0 + u;
-    const int nx = I.nx, ny = I.ny, nz = I.nz;
-    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
-    const E* src = (const E*)I.pop[step & 1];
-    const long long cs = 19 * N;
-    const T rho0 = (T)I.rho0;
-    T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const int sz = z - cz(i);
-        T r, b;
-        if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
-            S::load(src, cs, (long long)opp(i) * N + n, (T)wq(opp(i)), rho0, r, b);
-        } else if (sz >= nz) {
-            r = T(0);
-            b = (T)wq(i) * rho0;
-        } else {
-            const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
-            S::load(src, cs, (long long)i * N + ((long long)sz * ny + sy) * nx + sx, (T)wq(i),
-                    rho0, r, b);
-        }
-        rR += r;
-        rB += b;
-        const T F = r + b;
-        jx += cx(i) * F;
-        jy += cy(i) * F;
-        jz += cz(i) * F;
-    }
+    T m[5];
+    stream_moments<S>(I, step, n, m);
+    const T rR = m[0], rB = m[1], jx = m[2], jy = m[3], jz = m[4];
     if (diag) {
         double* d = diag + 5 * u;
         d[0] = rR;
@@ -1081,10 +1168,12 @@ __global__ void k_init_droplet(InstDev I, int shape, double cx_, double cy_, dou
         q = fabs(dx) > r ? fabs(dx) : r;
     }
     const double C = tanh(-(q - 1.0) * m / width);
-    E* p = (E*)I.pop[0];
-    for (int i = 0; i < 19; ++i)
-        S::from_f64(p, 19 * N, (long long)i * N + n, i, I.rho0, wq(i) * I.rho0 * (1.0 + C) / 2.0,
-                    wq(i) * I.rho0 * (1.0 - C) / 2.0);
+    for (int i = 0; i < 19; ++i) {
+        E* p;
+        long long cs, k;
+        post_place<S>(I, 0, i, n, p, cs, k);
+        S::from_f64(p, cs, k, i, I.rho0, wq(i) * I.rho0 * (1.0 + C) / 2.0, wq(i) * I.rho0 * (1.0 - C) / 2.0);
+    }
 }
 
 // Populations <-> FP64 staging: elements t0..t0+len of [19][N]; staging
@@ -1098,7 +1187,10 @@ __global__ void k_pop_to_f64(InstDev I, long long step, long long t0, long long 
     if (u >= len) return;
     const long long t = t0 + u;
     double r, b;
-    S::to_f64((const E*)I.pop[step & 1], 19 * N, t, (int)(t / N), I.rho0, r, b);
+    E* p;
+    long long cs, k;
+    post_place<S>(I, step, (int)(t / N), t % N, p, cs, k);
+    S::to_f64(p, cs, k, (int)(t / N), I.rho0, r, b);
     out[u] = r;
     out[len + u] = b;
 }
@@ -1110,7 +1202,10 @@ __global__ void k_pop_from_f64(InstDev I, long long step, long long t0, long lon
     const long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (u >= len) return;
     const long long t = t0 + u;
-    S::from_f64((E*)I.pop[step & 1], 19 * N, t, (int)(t / N), I.rho0, in[u], in[len + u]);
+    E* p;
+    long long cs, k;
+    post_place<S>(I, step, (int)(t / N), t % N, p, cs, k);
+    S::from_f64(p, cs, k, (int)(t / N), I.rho0, in[u], in[len + u]);
 }
 
 // Colour field of the next step, FP64
@@ -1159,7 +1254,10 @@ __global__ void k_mass(InstDev I, long long step, double* __restrict__ out) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 19 * N;
          t += (long long)gridDim.x * blockDim.x) {
         double r, b;
-        S::to_f64((const E*)I.pop[step & 1], 19 * N, t, (int)(t / N), I.rho0, r, b);
+        E* p;
+        long long cs, k;
+        post_place<S>(I, step, (int)(t / N), t % N, p, cs, k);
+        S::to_f64(p, cs, k, (int)(t / N), I.rho0, r, b);
         sr += r;
         sb += b;
     }

@@ -145,7 +145,15 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
         I.top_bc = c.top_bc;
         I.N = (long long)c.nx * c.ny * c.nz;
         const size_t eb = elem_bytes(c.prec), cb = comp_bytes(c.prec);
-        for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb);
+        I.inplace = c.inplace;
+        if (c.inplace) {
+            // one buffer read and written in place, plus the wall ghost slots
+            I.pop[0] = I.pop[1] = cv.take(2 * 19 * I.N * eb);
+            I.ghost = cv.take(2 * 10 * (size_t)c.nx * c.ny * eb);
+        } else {
+            for (int p = 0; p < 2; ++p) I.pop[p] = cv.take(2 * 19 * I.N * eb);
+            I.ghost = nullptr;
+        }
         for (int p = 0; p < 3; ++p) I.rho[p] = cv.take(2 * I.N * cb);
         I.cot = (double*)cv.take(sizeof(double) * c.nx * c.ny);
         I.hcol = cv.take(cb * c.nx * c.ny);
@@ -213,6 +221,7 @@ lbm_status check_config(const lbm_config& c) {
     if (!(c.rho0 > 0.0) || c.beta < 0.0 || c.beta > 1.0 || c.sigma < 0.0) return LBM_EINVAL;
     if (c.J0 < 0.0 || c.K <= 0.0) return LBM_EINVAL;
     if (c.top_bc != 0 && c.top_bc != 1) return LBM_EINVAL;
+    if (c.inplace != 0 && c.inplace != 1) return LBM_EINVAL;
     if (c.shape != 0 && c.shape != 1) return LBM_EINVAL;
     if (!(c.a > 0 && c.b > 0 && c.c > 0 && c.width > 0)) return LBM_EINVAL;
     if (!(c.theta_deg > 0.0 && c.theta_deg < 180.0)) return LBM_EINVAL;
@@ -245,6 +254,7 @@ struct lbm_handle {
     int shape = 0;  // index into SHAPES
     // the fused kernel may pull by bulk row copies (32- and 16-bit storage, every nx % 4 == 0)
     bool bulk = false;
+    bool inplace = false;  // esoteric-pull storage (every instance of the batch)
     // second stream of a step: column heights and the neighbour list run beside
     // the coupling-field pass (fork/join by events, captured into the graph)
     cudaStream_t side = nullptr;
@@ -282,12 +292,15 @@ constexpr size_t stage_bytes(int tx, int ty, bool bulk) {
 template <class S, int TX, int TY, int MINB>
 lbm_status prepare_one() {
     const size_t dyn = stage_bytes<S>(TX, TY, false);
-    if (dyn > 0)
-        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, false>,
+    if (dyn > 0) {
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, false, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    }
     if constexpr (S::WORDS > 0)
-        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stage_bytes<S>(TX, TY, true)));
+        CK(cudaFuncSetAttribute(k_stream_collide<S, TX, TY, MINB, true, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_bytes<S>(TX, TY, true)));
     return LBM_OK;
 }
 
@@ -307,20 +320,27 @@ lbm_status launch_fused(lbm_handle* h) {
     const InstDev* in = h->L.d_inst;
     const TileDesc* td = h->L.d_tiles;
     const bool bulk = S::WORDS > 0 && h->bulk && sh.bulk != 0;
+    constexpr bool W = S::WORDS != 0;
     if (sh.tx == 32 && sh.ty == 8 && sh.minb == 2) {
-        if (bulk)
-            k_stream_collide<S, 32, 8, 2, S::WORDS != 0><<<nb, 256, stage_bytes<S>(32, 8, true), h->stream>>>(
+        if (h->inplace)
+            k_stream_collide<S, 32, 8, 2, false, true><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(
+                in, td, h->L.glob);
+        else if (bulk)
+            k_stream_collide<S, 32, 8, 2, W, false><<<nb, 256, stage_bytes<S>(32, 8, true), h->stream>>>(
                 in, td, h->L.glob);
         else
-            k_stream_collide<S, 32, 8, 2, false><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(in, td,
-                                                                                                      h->L.glob);
+            k_stream_collide<S, 32, 8, 2, false, false><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(
+                in, td, h->L.glob);
     } else if (sh.tx == 32 && sh.ty == 4 && sh.minb == 4) {
-        if (bulk)
-            k_stream_collide<S, 32, 4, 4, S::WORDS != 0><<<nb, 128, stage_bytes<S>(32, 4, true), h->stream>>>(
+        if (h->inplace)
+            k_stream_collide<S, 32, 4, 4, false, true><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(
+                in, td, h->L.glob);
+        else if (bulk)
+            k_stream_collide<S, 32, 4, 4, W, false><<<nb, 128, stage_bytes<S>(32, 4, true), h->stream>>>(
                 in, td, h->L.glob);
         else
-            k_stream_collide<S, 32, 4, 4, false><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(in, td,
-                                                                                                      h->L.glob);
+            k_stream_collide<S, 32, 4, 4, false, false><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(
+                in, td, h->L.glob);
     } else {
         return LBM_EINVAL;
     }
@@ -793,7 +813,7 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
     for (int k = 0; k < n; ++k) {
         lbm_status st = check_config(cfgs[k]);
         if (st != LBM_OK) return st;
-        if (cfgs[k].prec != cfgs[0].prec) return LBM_EINVAL;
+        if (cfgs[k].prec != cfgs[0].prec || cfgs[k].inplace != cfgs[0].inplace) return LBM_EINVAL;
         if (cfgs[k].max_beads > 0 && cfgs[0].max_beads > 0 && cfgs[k].substeps != cfgs[0].substeps)
             return LBM_EINVAL;
     }
@@ -802,7 +822,8 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
     h->cfg.assign(cfgs, cfgs + n);
     h->stream = (cudaStream_t)stream;
     h->prec = cfgs[0].prec;
-    h->bulk = h->prec != LBM_FP64;
+    h->inplace = cfgs[0].inplace != 0;
+    h->bulk = h->prec != LBM_FP64 && !h->inplace;
     for (int k = 0; k < n; ++k) h->bulk = h->bulk && cfgs[k].nx % 4 == 0;
     Carver cv{(char*)dev_ws};
     carve(cfgs, n, cv, h->L);

@@ -306,6 +306,10 @@ using StoreB16 = StoreShift16<__nv_bfloat16, __half>;
 struct InstDev {
     int nx, ny, nz, top_bc;
     long long N;
+    // esoteric-pull in-place storage: one population buffer (pop[0] == pop[1]) plus
+    // ghost slots below z = 0 and above the top, [comp][side][5 pairs][ny][nx]
+    int inplace, pad3;
+    void* ghost;
     int t8x, t8y, t8z;           // 8^3 coupling-tile grid
     int pad0;
     void* pop[2];                // population buffers (storage type)
@@ -361,6 +365,89 @@ struct InstDev {
     int* csr_col;                // [2 max_edges]
     double* csr_val;             // [2 max_edges] conductances
 };
+
+// ---------------------------------------------------------------------------
+// Esoteric-pull in-place storage (one buffer, read and written in place).  The
+// directions pair up as (i, i+1), i odd, c_{i+1} = -c_i.  At a step of parity
+// p = step & 1 a node reads the streamed f_i from its own slot (p ? i : i+1) and
+// f_{i+1} from slot (p ? i+1 : i) of its neighbour n + c_i, and writes the
+// post-collision f*_i to slot (p ? i+1 : i) of n + c_i and f*_{i+1} to its own
+// slot (p ? i : i+1): every slot is read and written by one node per step, so
+// the step needs no second buffer.  At the walls the neighbour n + c_i may not
+// exist: f*_i then goes to a ghost slot of the node's column (side 0 below z = 0,
+// 1 above the top), from which the bounced f_{i+1} is read next step; the f_i
+// bounced from the other side is read from the node's other own slot, where the
+// previous step left f*_{i+1}.  Under the gas top the inflow replaces the
+// downward populations, and the outflow of the previous step is read (for the
+// FP64 budget) from the top ghost (odd members) or the other own slot (even).
+// ---------------------------------------------------------------------------
+// ghost pair of the odd member of a pair with c_z != 0
+__host__ __device__ constexpr int ghost_pair(int i) {
+    return i == 5 ? 0 : (i == 11 ? 1 : (i == 13 ? 2 : (i == 15 ? 3 : 4)));
+}
+// a population's place: element index k into the main buffer (comp stride 19 N)
+// or, with ghost set, into the ghost array (comp stride 10 nx ny)
+struct PopLoc {
+    unsigned k;
+    bool ghost;
+};
+__host__ __device__ __forceinline__ int wrap_one(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__host__ __device__ __forceinline__ unsigned ghost_index(int side, int g, int x, int y, int nx, int ny) {
+    return (unsigned)((side * 5 + g) * ny + y) * nx + x;
+}
+// where the post-collision population i of node (x, y, z) goes at a step of parity p
+__host__ __device__ __forceinline__ PopLoc ep_store(int i, int x, int y, int z, int p, int nx, int ny, int nz) {
+    const unsigned nxy = (unsigned)nx * ny, N = nxy * (unsigned)nz;
+    if (i == 0) return {(unsigned)z * nxy + (unsigned)y * nx + x, false};
+    if (i & 1) {
+        const int tz = z + cz(i);
+        if (tz < 0) return {ghost_index(0, ghost_pair(i), x, y, nx, ny), true};
+        if (tz >= nz) return {ghost_index(1, ghost_pair(i), x, y, nx, ny), true};
+        const unsigned slot = p ? i + 1 : i;
+        return {slot * N + (unsigned)tz * nxy + (unsigned)wrap_one(y + cy(i), ny) * nx + wrap_one(x + cx(i), nx),
+                false};
+    }
+    const unsigned slot = p ? i - 1 : i;
+    return {slot * N + (unsigned)z * nxy + (unsigned)y * nx + x, false};
+}
+// where the streamed population i of node (x, y, z) is read at a step of parity p;
+// false: replaced by the gas inflow (loc is then a harmless own slot)
+__host__ __device__ __forceinline__ bool ep_load(int i, int x, int y, int z, int p, int nx, int ny, int nz,
+                                                 int top_bc, PopLoc& loc) {
+    const unsigned nxy = (unsigned)nx * ny, N = nxy * (unsigned)nz;
+    const unsigned node = (unsigned)z * nxy + (unsigned)y * nx + x;
+    loc = {node, false};
+    if (i == 0) return true;
+    if (i & 1) {
+        const int sz = z - cz(i);
+        if (sz >= nz && top_bc == 1) return false;
+        const bool bounce = sz < 0 || sz >= nz;  // from the node's other own slot
+        const unsigned slot = (p != 0) != bounce ? i : i + 1;
+        loc = {slot * N + node, false};
+        return true;
+    }
+    const int j = i - 1;  // the odd member: f_i comes from n + c_j
+    const int tz = z + cz(j);
+    if (tz < 0) {
+        loc = {ghost_index(0, ghost_pair(j), x, y, nx, ny), true};
+        return true;
+    }
+    if (tz >= nz) {
+        if (top_bc == 1) return false;
+        loc = {ghost_index(1, ghost_pair(j), x, y, nx, ny), true};
+        return true;
+    }
+    const unsigned slot = p ? i : j;
+    loc = {slot * N + (unsigned)tz * nxy + (unsigned)wrap_one(y + cy(j), ny) * nx + wrap_one(x + cx(j), nx), false};
+    return true;
+}
+// the previous step's outflow through the gas top, direction i (c_z(i) > 0), column (x, y)
+__host__ __device__ __forceinline__ PopLoc ep_outflow(int i, int x, int y, int p, int nx, int ny, int nz) {
+    if (i & 1) return {ghost_index(1, ghost_pair(i), x, y, nx, ny), true};
+    const unsigned nxy = (unsigned)nx * ny;
+    const unsigned slot = p ? i : i - 1;
+    return {slot * nxy * (unsigned)nz + (unsigned)(nz - 1) * nxy + (unsigned)y * nx + x, false};
+}
 
 struct StepGlobals {
     long long step;

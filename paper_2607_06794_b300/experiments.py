@@ -50,7 +50,7 @@ def e1_drying(steps=20000, every=500, prec="fp32", theta_r=30.0, J0=None):
     return out
 
 
-def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=None, wires=None):
+def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=None, wires=None, report=None):
     """Run the workload `make(prec)` at each precision for `steps` steps.
 
     wires: per instance (centres, directions, beads per wire) placed identically in
@@ -65,9 +65,22 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
             if th is not None:
                 sim.set_substrate_pattern(k, th)
         if wires is None:
+            # the first run places the wires (seeded, inside its liquid); the later runs take
+            # the same wires, rebuilt from the first run's bead positions
             for k, w in enumerate(wl.wires):
                 if w is not None and w[0] > 0:
                     sim.add_nanowires(k, w[0], w[1], seed=wl.cfgs[k].seed)
+            wires = [None] * len(wl.cfgs)
+            for k, w in enumerate(wl.wires):
+                if w is not None and w[0] > 0:
+                    c = wl.cfgs[k]
+                    nbf = max(1, int(round(w[1] / c.d0)))
+                    X = sim.read(k, "bead_x").reshape(w[0], nbf, 3)
+                    d = X[:, -1] - X[:, 0]
+                    d[:, 0] -= c.nx * np.round(d[:, 0] / c.nx)
+                    d[:, 1] -= c.ny * np.round(d[:, 1] / c.ny)
+                    cen = X[:, 0] + 0.5 * d
+                    wires[k] = (cen, d, nbf)
         else:
             for k, pw in enumerate(wires):
                 if pw is not None:
@@ -87,22 +100,37 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
         desc = sim.descriptors(0) if any(w is not None for w in (wires or wl.wires)) else None
         out[prec] = {"series": rec, "final": rec[-1], "descriptors": desc, "status": sim.status()}
         sim.close()
+        if report is not None:
+            report(prec, out[prec])
     return out
 
 
 def main(argv=None):
     """python -m paper_2607_06794_b300.experiments [--steps N] [--every K] [--J0 J] [--theta_r T]:
-    prints one JSON line per record of the E1 drying run."""
+    prints one JSON line per record of the E1 drying run.
+    python -m paper_2607_06794_b300.experiments --compare c5 [--precs fp64,fp32,fp16] --steps N:
+    runs that workload at each storage precision with the same wires and prints, per
+    precision, the droplet observables along the run and the deposit descriptors."""
     import argparse
     import json
 
     ap = argparse.ArgumentParser()
+    ap.add_argument("--compare", default=None)
+    ap.add_argument("--precs", default="fp64,fp32,fp16")
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--every", type=int, default=500)
     ap.add_argument("--prec", default="fp32")
     ap.add_argument("--theta_r", type=float, default=30.0)
     ap.add_argument("--J0", type=float, default=None)
     a = ap.parse_args(argv)
+    if a.compare:
+        def show(prec, r):
+            print(json.dumps({"precision": prec, "status": r["status"], "descriptors": r["descriptors"],
+                              "series": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
+                                         for e in r["series"]]}), flush=True)
+        storage_comparison(workloads.WORKLOADS[a.compare], tuple(a.precs.split(",")), a.steps, a.every,
+                           report=show)
+        return
     r = e1_drying(a.steps, a.every, a.prec, a.theta_r, a.J0)
     for k in range(len(r["step"])):
         print(json.dumps({key: (int(r[key][k]) if key == "step" else round(float(r[key][k]), 6))

@@ -69,7 +69,7 @@ def test_workspace_size_needs_no_gpu(lib):
 
 @pytest.mark.parametrize("bad", [dict(nz=1), dict(tau_R=0.5), dict(prec=7), dict(theta_deg=0.0),
                                  dict(top_bc=3), dict(a=0.0), dict(K=0.0), dict(beta=2.0),
-                                 dict(max_beads=10, Rm=1.0)])
+                                 dict(max_beads=10, Rm=1.0), dict(inplace=2)])
 def test_invalid_configs_are_rejected_before_any_device_call(lib, bad):
     from paper_2607_06794_b300 import Config, _lib
     import dataclasses
@@ -89,3 +89,15 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_destroy(None) == _lib.EINVAL
     assert lib.lbm_workspace_bytes(None, 1) == 0
     assert not math.isnan(0.0)
+
+
+def test_inplace_storage_takes_one_population_buffer(lib):
+    """Esoteric-pull storage needs one population buffer plus the wall ghost slots instead of
+    two buffers (workspace size, computed without a GPU)."""
+    from paper_2607_06794_b300 import Config, workspace_bytes
+    for prec, eb in (("fp64", 8), ("fp32", 4), ("fp16", 2)):
+        c = Config(64, 48, 40, prec=prec)
+        two = workspace_bytes([c])
+        c.inplace = 1
+        one = workspace_bytes([c])
+        assert abs((two - one) - (2 * 19 * 64 * 48 * 40 * eb - 2 * 10 * 64 * 48 * eb)) <= 1024
