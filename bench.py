@@ -533,6 +533,14 @@ def main():
             v = measure(workloads.droplet_c5(vp), wires, args.steps)
             v["speedup_vs_fp32_same_workload"] = round(v["value"] / value, 3)
             variants[vp] = v
+        # in-place (esoteric-pull) population storage: half the population memory
+        for vp in ("fp32", "fp16"):
+            w5 = workloads.droplet_c5(vp)
+            for c in w5.cfgs:
+                c.inplace = 1
+            v = measure(w5, wires, args.steps)
+            v["speedup_vs_fp32_same_workload"] = round(v["value"] / value, 3)
+            variants[vp + "_inplace"] = v
         # the batched sweep: 64 uneven lattices with wires, one launch per step, FP16 and FP32
         k4 = max(20, args.steps // 4)
         c4 = {}

@@ -27,7 +27,8 @@ namespace {
 // fills the GPU"; chunks above nz take the whole column), and the register
 // budget as resident blocks per SM (128 registers a thread: 4 blocks of 32x4,
 // 2 of 32x8; a 96-register form of 32x4 at 5 blocks per SM measured 5-40 %
-// slower on every workload and was dropped), and how 32- and 16-bit storage
+// slower on every workload, a spill-free 168-register form at 3 blocks 6-16 %
+// slower, and both were dropped), and how 32- and 16-bit storage
 // stages the pull (0: per-element asynchronous copies; 1: bulk row copies where
 // every lattice of the batch has nx % 4 == 0, else per-element).  Blocks of equal
 // chunks march up in step, so the halo planes a block re-reads were just read by

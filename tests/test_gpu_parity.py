@@ -455,6 +455,39 @@ def test_checkpoint_restore_with_beads_continues_the_run(lbm, oracle):
     assert np.max(np.abs(pa - pb)) < 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_16bit_restore_continues_up_to_the_rounding_of_the_stored_words(lbm, oracle, prec):
+    """A 16-bit run pushes the next step's moments from the values before rounding, while a
+    restore rebuilds them from the stored (rounded) words, so the restored run continues the
+    unbroken one only up to that rounding: after 3 more steps the populations agree to the
+    16-bit tolerance of the one-step parity test, the beads to 1e-5."""
+    cfg = droplet_cfg(lbm, nx=48, ny=32, nz=20, prec=prec, max_beads=40, xi=0.02, a=18, b=11, c=14,
+                      J0=1e-3, evap_start=0)
+    fil, pos, X = bead_case(cfg, seed=31, n_fil=4)
+    cen = X.reshape(4, 4, 3).mean(axis=1)
+    dirs = X.reshape(4, 4, 3)[:, -1] - X.reshape(4, 4, 3)[:, 0]
+    a = lbm.Simulation([cfg])
+    a.add_nanowires(0, 4, 8.0, cen, dirs)
+    a.step(4)
+    saved = {f: a.read(0, f) for f in ("accum", "populations", "bead_x", "bead_v", "bead_f")}
+    b = lbm.Simulation([cfg])
+    b.write(0, "accum", saved["accum"])
+    b.write(0, "populations", saved["populations"])
+    b.add_nanowires(0, 4, 8.0, cen, dirs)
+    for f in ("bead_x", "bead_v", "bead_f"):
+        b.write(0, f, saved[f])
+    # the FP64 host form re-encodes to the same words up to the host's recomputation of the
+    # liquid fraction, whose last bit can move where the fraction is near zero
+    sp = saved["populations"]
+    assert pop_err(b.read(0, "populations"), sp[0], sp[1]) < 1e-6
+    a.step(3)
+    b.step(3)
+    assert b.status() == 0 and a.status() == 0
+    pa, pb = a.read(0, "populations"), b.read(0, "populations")
+    assert pop_err(pb, pa[0], pa[1]) < TOL[prec]
+    assert np.allclose(b.read(0, "bead_x"), a.read(0, "bead_x"), rtol=0, atol=1e-5)
+
+
 def test_tall_lattice_with_beads_in_the_upper_chunk(lbm, oracle):
     """nz = 300 is split into z-chunks (at most 240 planes each) whose coupling-tile flags the
     fused kernel keeps in a bit mask per column; wires near z = 280 exercise the upper chunk."""
