@@ -188,10 +188,11 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts, const StepGlobal
 }
 
 // u* = (j + (F_s + body)/2)/rho and grad C on the nodes of flagged tiles.
-template <class S>
+template <class S, bool EP>
 __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobals* __restrict__ glob, int t);
 
-template <class S>
+// EP: the populations are stored in place (esoteric pull), else in two buffers
+template <class S, bool EP>
 __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ insts,
                                                     const StepGlobals* __restrict__ glob) {
     using T = typename S::T;
@@ -201,12 +202,12 @@ __global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ 
     const int p = (int)(__ldcg(&glob->step) & 1);
     const int ntl = *tcount_of(*Ip, p);
     for (int it = blockIdx.x; it < ntl; it += gridDim.x) {
-        bead_field_tile<S>(Ip, glob, tlist_of(*Ip, p)[it]);
+        bead_field_tile<S, EP>(Ip, glob, tlist_of(*Ip, p)[it]);
         __syncthreads();
     }
 }
 
-template <class S>
+template <class S, bool EP>
 __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobals* __restrict__ glob, int t) {
     using T = typename S::T;
     using E = typename S::E;
@@ -216,6 +217,7 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     const long long step = __ldcg(&glob->step);
     const T* rho = (const T*)I.rho[step % 3];
     const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
     const int X0 = (t % I.t8x) * 8, Y0 = ((t / I.t8x) % I.t8y) * 8, Z0 = (t / (I.t8x * I.t8y)) * 8;
     const int tid = threadIdx.x;
     __syncthreads();  // shared blocks of the previous tile are free
@@ -228,7 +230,7 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
         T c = T(0);
         if (z >= 0 && z <= nz) {
             const int x = wrap_near(X0 - 2 + lx, nx), y = wrap_near(Y0 - 2 + ly, ny);
-            c = colour_of(rho, I.N, ((long long)(z < nz ? z : nz - 1) * ny + y) * nx + x);
+            c = colour_of(rho, N, ((long long)(z < nz ? z : nz - 1) * ny + y) * nx + x);
         }
         sC[lz][ly][lx] = c;
     }
@@ -328,10 +330,11 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     const T hs = T(0.5) * (T)I.sigma;
     const T rho0 = (T)I.rho0;
     T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+    const NodePull<S, EP> pl(I, step, x, y, z);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         T r, b;
-        pull_streamed<S>(I, step, i, x, y, z, r, b);
+        pl.pull(i, r, b);
         rR += r;
         rB += b;
         const T F = r + b;

@@ -1034,42 +1034,58 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 // and after populations are written from the host.  Writes rho[pr] (both
 // components) and clears the next buffer.
 // ---------------------------------------------------------------------------
-// The streamed population i of node (x, y, z) at `step` in the compute type, under
+// The streamed populations of node (x, y, z) at `step` in the compute type, under
 // either storage layout (two buffers: pulled from x - c_i of the buffer of the step's
-// parity, bounced back at the walls, gas equilibrium from above the gas top).
-template <class S>
-__device__ __forceinline__ void pull_streamed(const InstDev& I, long long step, int i, int x, int y, int z,
-                                              typename S::T& r, typename S::T& b) {
+// parity, bounced back at the walls, gas equilibrium from above the gas top; in place:
+// ep_load, chosen at compile time by EP).  The instance's fields are read once per
+// node, then pull(i) per direction.
+template <class S, bool EP>
+struct NodePull {
     using T = typename S::T;
     using E = typename S::E;
-    const T rho0 = (T)I.rho0;
-    const int nx = I.nx, ny = I.ny, nz = I.nz;
-    if (I.inplace) {
-        PopLoc L;
-        if (!ep_load(i, x, y, z, (int)(step & 1), nx, ny, nz, I.top_bc, L)) {
-            r = T(0);
-            b = (T)wq(i) * rho0;
+    const E* src;
+    const E* gslot;
+    unsigned N, cs, gcs, node;
+    int nx, ny, nz, top_bc, x, y, z, p;
+    T rho0;
+    __device__ __forceinline__ NodePull(const InstDev& I, long long step, int x_, int y_, int z_)
+        : x(x_), y(y_), z(z_) {
+        nx = I.nx;
+        ny = I.ny;
+        nz = I.nz;
+        top_bc = I.top_bc;
+        N = (unsigned)I.N;
+        cs = 19u * N;
+        gcs = 10u * (unsigned)nx * ny;
+        p = (int)(step & 1);
+        src = (const E*)I.pop[EP ? 0 : p];
+        gslot = (const E*)I.ghost;
+        rho0 = (T)I.rho0;
+        node = ((unsigned)z * ny + y) * nx + x;
+    }
+    __device__ __forceinline__ void pull(int i, T& r, T& b) const {
+        if constexpr (EP) {
+            PopLoc L;
+            if (!ep_load(i, x, y, z, p, nx, ny, nz, top_bc, L)) {
+                r = T(0);
+                b = (T)wq(i) * rho0;
+                return;
+            }
+            S::load(L.ghost ? gslot : src, L.ghost ? gcs : cs, L.k, (T)wq(i), rho0, r, b);
             return;
         }
-        const E* base = L.ghost ? (const E*)I.ghost : (const E*)I.pop[0];
-        S::load(base, L.ghost ? 10u * (unsigned)nx * ny : 19u * (unsigned)I.N, L.k, (T)wq(i), rho0, r, b);
-        return;
+        const int sz = z - cz(i);
+        if (sz < 0 || (sz >= nz && top_bc == 0)) {
+            S::load(src, cs, (unsigned)opp(i) * N + node, (T)wq(opp(i)), rho0, r, b);
+        } else if (sz >= nz) {
+            r = T(0);
+            b = (T)wq(i) * rho0;
+        } else {
+            const int sx = wrap_one(x - cx(i), nx), sy = wrap_one(y - cy(i), ny);  // shifts of one cell
+            S::load(src, cs, (unsigned)i * N + ((unsigned)sz * ny + sy) * nx + sx, (T)wq(i), rho0, r, b);
+        }
     }
-    const long long N = I.N;
-    const E* src = (const E*)I.pop[step & 1];
-    const unsigned cs = 19u * (unsigned)N;
-    const long long node = ((long long)z * ny + y) * nx + x;
-    const int sz = z - cz(i);
-    if (sz < 0 || (sz >= nz && I.top_bc == 0)) {
-        S::load(src, cs, (unsigned)((long long)opp(i) * N + node), (T)wq(opp(i)), rho0, r, b);
-    } else if (sz >= nz) {
-        r = T(0);
-        b = (T)wq(i) * rho0;
-    } else {
-        const int sx = wrapi(x - cx(i), nx), sy = wrapi(y - cy(i), ny);
-        S::load(src, cs, (unsigned)((long long)i * N + ((long long)sz * ny + sy) * nx + sx), (T)wq(i), rho0, r, b);
-    }
-}
+};
 
 // Where the post-collision population i of node n, as left by the step before
 // `step`, is stored: base pointer, component stride and element index.
@@ -1092,16 +1108,16 @@ __device__ __forceinline__ void post_place(const InstDev& I, long long step, int
 }
 
 // rho_R, rho_B, j of node n from the populations that stream into it at `step`
-template <class S>
-__device__ void stream_moments(const InstDev& I, long long step, long long n, typename S::T* m) {
+template <class S, bool EP>
+__device__ void stream_moments_t(const InstDev& I, long long step, int x, int y, int z,
+                                 typename S::T* m) {
     using T = typename S::T;
-    const int nx = I.nx, ny = I.ny;
-    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
     T rR = 0, rB = 0, jx = 0, jy = 0, jz = 0;
+    const NodePull<S, EP> pl(I, step, x, y, z);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         T r, b;
-        pull_streamed<S>(I, step, i, x, y, z, r, b);
+        pl.pull(i, r, b);
         rR += r;
         rB += b;
         const T F = r + b;
@@ -1114,6 +1130,16 @@ __device__ void stream_moments(const InstDev& I, long long step, long long n, ty
     m[2] = jx;
     m[3] = jy;
     m[4] = jz;
+}
+
+template <class S>
+__device__ void stream_moments(const InstDev& I, long long step, long long n, typename S::T* m) {
+    const int nx = I.nx, ny = I.ny;
+    const int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long long)nx * ny));
+    if (I.inplace)
+        stream_moments_t<S, true>(I, step, x, y, z, m);
+    else
+        stream_moments_t<S, false>(I, step, x, y, z, m);
 }
 
 template <class S>

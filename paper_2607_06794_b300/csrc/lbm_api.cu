@@ -399,7 +399,11 @@ lbm_status launch_bead_step(lbm_handle* h, cudaEvent_t before, cudaEvent_t after
     CK(cudaEventRecord(h->ev_side, h->side));
     int maxt = 0;
     for (auto& I : h->L.inst) maxt = std::max(maxt, I.ntile);
-    k_bead_field<S><<<dim3(std::min(maxt, 2 * 148), n), 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
+    const dim3 fgrid(std::min(maxt, 2 * 148), n);
+    if (h->inplace)
+        k_bead_field<S, true><<<fgrid, 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
+    else
+        k_bead_field<S, false><<<fgrid, 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
     const int S_ = h->cfg[0].substeps;
     // blocks of 64 threads, so that the FP64 integration and the stencils of a few
     // hundred beads spread over many SMs; sixteen lanes per bead up to 2048 beads in
