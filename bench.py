@@ -38,13 +38,17 @@ ALG_BYTES = {"fp64": 640, "fp32": 320, "fp16": 168, "bf16": 168}
 # taken, the workload and the tiling; null once any of them differs.  The DRAM
 # counters take more than one replay pass, which the 5 GB of the 512x256x128
 # lattice rules out, so its figure is the 256x128x64 capture (same kernel, same
-# 32x4 columns) scaled by the node count (8x): that capture moved 1.004 times its
+# 32x4 columns; on that lattice the mixed tiling 13 is the 32-plane chunks of
+# tiling 6) scaled by the node count (8x): that capture moved 1.005 times its
 # algorithmic bytes, and a launch's traffic grows with the nodes it updates.
-_C2_TRAFFIC = 367363328 + 306353408
+_C2_TRAFFIC = 367757056 + 306613760
+_C5 = "c5_512x256x128_periodic_stripes_2000wires"
 TRAFFIC = {
-    ("14c8e0a0ccf1", "c2_256x128x64_stripe_200wires", 6): _C2_TRAFFIC,
-    ("14c8e0a0ccf1", "c5_512x256x128_periodic_stripes_2000wires", 6): 8 * _C2_TRAFFIC,
-    ("14c8e0a0ccf1", "c5_512x256x128_periodic_stripes_2000wires", 4): 8 * _C2_TRAFFIC,
+    ("d1c127fe6e33", "c2_256x128x64_stripe_200wires", 13): _C2_TRAFFIC,
+    ("d1c127fe6e33", "c2_256x128x64_stripe_200wires", 6): _C2_TRAFFIC,
+    ("d1c127fe6e33", _C5, 13): 8 * _C2_TRAFFIC,
+    ("d1c127fe6e33", _C5, 6): 8 * _C2_TRAFFIC,
+    ("d1c127fe6e33", _C5, 4): 8 * _C2_TRAFFIC,
 }
 
 
@@ -412,6 +416,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tiling", type=int, default=None,
                     help="use this candidate tiling of the fused kernel instead of autotuning")
+    ap.add_argument("--inplace", action="store_true",
+                    help="store the populations in place (one buffer, esoteric pull)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -434,6 +440,9 @@ def main():
 
     mk = workloads.WORKLOADS[args.workload]
     wl = mk(args.prec) if args.prec else mk("fp32") if args.workload in ("c5", "c4") else mk()
+    if args.inplace:
+        for c in wl.cfgs:
+            c.inplace = 1
     prec = wl.cfgs[0].prec
     wires = wire_placement(wl)
     sim, tuned = prepared(wl, wires, args)
@@ -594,8 +603,10 @@ def main():
             "data": "synthetic",
             "config": {"workload": wl.name, "lattice": [c.nx, c.ny, c.nz], "precision": prec,
                        "nanowires": wl.wires[0][0] if wl.wires[0] else 0,
+                       "storage": "in place" if args.inplace else "two buffers",
                        "l2": "inputs larger than L2 (population buffers "
-                             f"{2 * 19 * wl.nodes * {'fp64': 8, 'fp32': 4}.get(prec, 2) / 1e6:.0f} MB x2)",
+                             f"{2 * 19 * wl.nodes * {'fp64': 8, 'fp32': 4}.get(prec, 2) / 1e6:.0f} MB "
+                             f"x{1 if args.inplace else 2})",
                        "parallelism": f"replicas x{world}",
                        "tiling": None if tuned is None else tuned[0]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

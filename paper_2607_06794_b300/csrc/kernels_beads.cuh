@@ -25,22 +25,44 @@ __device__ __forceinline__ T lj_shape_dr(T d0, T r) {
     return (T(-12) * s6 * s6 + T(12) * s6) / r;
 }
 
+// Force parameters of an instance in the compute type: the FP64 values, or their
+// FP32 roundings made on the host (the same values a conversion here would give).
+// has_coh / has_s: cohesion / substrate adhesion on (tested in FP64).
+template <typename T>
+struct BeadPar {
+    T ks, Rm2, d0, eps_wca, kb, eps_coh, eps_s, rc, gamma, xi, mu, gamma_t, dt;
+    bool has_coh, has_s;
+    __device__ __forceinline__ explicit BeadPar(const InstDev& I) {
+        if constexpr (sizeof(T) == 8) {
+            ks = I.ks, Rm2 = I.Rm * I.Rm, d0 = I.d0, eps_wca = I.eps_wca, kb = I.kb, eps_coh = I.eps_coh;
+            eps_s = I.eps_s, rc = I.rc, gamma = I.gamma, xi = I.xi, mu = I.mu, gamma_t = I.gamma_t;
+            dt = I.dt_sub;
+        } else {
+            ks = I.f_ks, Rm2 = I.f_Rm2, d0 = I.f_d0, eps_wca = I.f_eps_wca, kb = I.f_kb;
+            eps_coh = I.f_eps_coh, eps_s = I.f_eps_s, rc = I.f_rc, gamma = I.f_gamma, xi = I.f_xi;
+            mu = I.f_mu, gamma_t = I.f_gamma_t, dt = I.f_dt_sub;
+        }
+        has_coh = I.eps_coh > 0.0;
+        has_s = I.eps_s > 0.0;
+    }
+};
+
 // dU/dr of a bead pair; `sep` = |index difference| if same filament, else 0
 template <typename T>
-__device__ __forceinline__ T pair_dUdr(const InstDev& I, bool same, int sep, T r, int& err) {
+__device__ __forceinline__ T pair_dUdr(const BeadPar<T>& bp, bool same, int sep, T r, int& err) {
     T f = 0;
-    const T d0 = (T)I.d0;
+    const T d0 = bp.d0;
     if (same && sep == 1) {  // FENE, Eq. (9)
-        T q = r * r / (T)(I.Rm * I.Rm);
+        T q = r * r / bp.Rm2;
         if (q >= T(1)) {
             err |= ERR_FENE;
             q = T(0.99);
         }
-        f += (T)I.ks * r / (T(1) - q);
+        f += bp.ks * r / (T(1) - q);
     }
-    if (same && sep == 2) f += (T)I.kb * (r - T(2) * d0);  // bending, Eq. (11)
-    if (r <= d0) f += (T)I.eps_wca * lj_shape_dr<T>(d0, r);  // WCA, Eq. (10)
-    if (!same && I.eps_coh > 0.0 && r > d0 && r < (T)I.rc) f += (T)I.eps_coh * lj_shape_dr<T>(d0, r);
+    if (same && sep == 2) f += bp.kb * (r - T(2) * d0);  // bending, Eq. (11)
+    if (r <= d0) f += bp.eps_wca * lj_shape_dr<T>(d0, r);  // WCA, Eq. (10)
+    if (!same && bp.has_coh && r > d0 && r < bp.rc) f += bp.eps_coh * lj_shape_dr<T>(d0, r);
     return f;
 }
 
@@ -443,20 +465,24 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
     return v;
 }
 
-// Force evaluation of sub-step s (1-based), L lanes per bead (8 or 16): the
+// Force evaluation of sub-step s (1-based), L lanes per bead (4, 8 or 16): the
 // lanes share the bonded partners and the neighbour list (pair forces in the
-// compute type); lanes 0..7 take one stencil node each for the interpolation
-// of u* and grad C and for the reaction spread; the group's
-// first lane adds drag, solvation, adhesion and friction and integrates in
-// FP64 (second half kick; if not last, the next first half kick and drift).
+// compute type) and the eight nodes of the trilinear stencil (8 / L each below
+// eight lanes, else lanes 0..7 one each) for the interpolation of u* and grad C
+// and for the reaction spread; every lane adds drag, solvation, adhesion and
+// friction, and lanes 0..2 integrate one component each in FP64 (second half
+// kick; if not last, the next first half kick and drift).  B300's FP64 pipe is
+// narrow, so the FP64 work per bead is what sets the pace: fewer lanes per bead
+// share the per-bead FP64 steps (stencil cell, constants, integration) among
+// more beads per warp.
 template <typename T, int L>
 __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __restrict__ glob, int s) {
-    static_assert(L >= 8 && L <= 32 && (L & (L - 1)) == 0, "8, 16 or 32 lanes per bead");
+    static_assert(L >= 4 && L <= 32 && (L & (L - 1)) == 0, "4, 8, 16 or 32 lanes per bead");
+    constexpr int CPL = L >= 8 ? 1 : 8 / L;  // stencil corners per lane
     const InstDev I = insts[blockIdx.y];
     const long long step = __ldcg(&glob->step);
     if (s == I.substeps && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) glob->bead_next = step + 1;
     const int lane = threadIdx.x & (L - 1);
-    const bool corner = lane < 8;  // lanes 0..7 take the eight trilinear corners
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (threadIdx.x & (32 - L)));
     const int a = (blockIdx.x * blockDim.x + threadIdx.x) / L;
     if (a >= I.nb) return;  // a whole group leaves together
@@ -464,26 +490,34 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     const double* cur = (s & 1) ? I.bx2 : I.bx;
     double* nxt = (s & 1) ? I.bx : I.bx2;
     const double dt = I.dt_sub, hk = I.hk_sub;
+    const BeadPar<T> bp(I);
     int err = 0;
     const double P[3] = {cur[3 * a], cur[3 * a + 1], cur[3 * a + 2]};
     const int fa = I.bfil[a], pa = I.bpos[a];
     const int nn = I.nnbr[a];
     // loads that do not depend on the pair loop go first, so that their latency overlaps it:
-    // this lane's stencil corner with u*, grad C and the tile flag there, the half-step velocity
-    long long idl = 0;
-    T wdl = 0;
-    int tl = 0;
-    T u[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
-    unsigned flagged = 1u;
-    if (corner) {
-        stencil_corner(I, P, lane, idl, wdl, tl);
-        const T* ust = (const T*)I.ust + 3 * idl;
-        const T* gcl = (const T*)I.gcol + 3 * idl;
-        for (int d = 0; d < 3; ++d) {
-            u[d] = ust[d];
-            gc[d] = gcl[d];
+    // this lane's stencil corners with u*, grad C and the tile flag there, the half-step velocity
+    long long idl[CPL];
+    T wdl[CPL], uc[CPL][3], gcc[CPL][3];
+    unsigned flagged[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int c = lane + k * L;
+        idl[k] = 0;
+        wdl[k] = 0;
+        flagged[k] = 1u;
+        for (int d = 0; d < 3; ++d) uc[k][d] = gcc[k][d] = 0;
+        if (c < 8) {
+            int tl = 0;
+            stencil_corner(I, P, c, idl[k], wdl[k], tl);
+            const T* ust = (const T*)I.ust + 3 * idl[k];
+            const T* gcl = (const T*)I.gcol + 3 * idl[k];
+            for (int d = 0; d < 3; ++d) {
+                uc[k][d] = ust[d];
+                gcc[k][d] = gcl[d];
+            }
+            flagged[k] = tflag_of(I, (int)(step & 1))[tl];
         }
-        flagged = tflag_of(I, (int)(step & 1))[tl];
     }
     const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     // ---- pair forces, candidates spread over the lanes ----
@@ -517,7 +551,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
         }
         const T d2 = (T)(cur[3 * b + 2] - P[2]);
         const T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-        const T g = pair_dUdr<T>(I, same, sep, r, err);
+        const T g = pair_dUdr<T>(bp, same, sep, r, err);
         if (g != T(0)) {
             const T gr = g / r;
             fx += gr * d0;
@@ -528,70 +562,85 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     fx = group_sum<L>(fx, gmask);
     fy = group_sum<L>(fy, gmask);
     fz = group_sum<L>(fz, gmask);
-    // ---- interpolation of u* and grad C, one stencil node per lane ----
-    {
-        const T wl = (T)wdl;
-        for (int d = 0; d < 3; ++d) {
-            u[d] = group_sum<L>(wl * u[d], gmask);
-            gc[d] = group_sum<L>(wl * gc[d], gmask);
+    // ---- interpolation of u* and grad C over the lanes' stencil corners ----
+    T u[3], gc[3];
+    for (int d = 0; d < 3; ++d) {
+        T su = 0, sg = 0;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            su += wdl[k] * uc[k][d];
+            sg += wdl[k] * gcc[k][d];
         }
+        u[d] = group_sum<L>(su, gmask);
+        gc[d] = group_sum<L>(sg, gmask);
     }
     T drag[3];
-    for (int d = 0; d < 3; ++d) drag[d] = (T)I.gamma * (u[d] - (T)vh[d]);
-    T f[3] = {fx + drag[0] + (T)I.xi * gc[0], fy + drag[1] + (T)I.xi * gc[1], fz + drag[2] + (T)I.xi * gc[2]};
+    for (int d = 0; d < 3; ++d) drag[d] = bp.gamma * (u[d] - (T)vh[d]);
+    T f[3] = {fx + drag[0] + bp.xi * gc[0], fy + drag[1] + bp.xi * gc[1], fz + drag[2] + bp.xi * gc[2]};
     // ---- substrate adhesion (LJ at the image distance) and load-dependent friction ----
     const T rw = T(2) * ((T)P[2] + T(0.5));
     T fw = 0;
-    if (I.eps_s > 0.0 && rw < (T)I.rc && rw > T(0)) fw = T(-2) * (T)I.eps_s * lj_shape_dr<T>((T)I.d0, rw);
-    if (I.eps_s > 0.0 && rw < (T)I.rc) {
+    if (bp.has_s && rw < bp.rc && rw > T(0)) fw = T(-2) * bp.eps_s * lj_shape_dr<T>(bp.d0, rw);
+    if (bp.has_s && rw < bp.rc) {
         const T load = (f[2] < T(0) ? -f[2] : T(0)) + (fw < T(0) ? -fw : T(0));
         const T vx = (T)vh[0], vy = (T)vh[1];
         const T vt = sqrt(vx * vx + vy * vy);
         if (vt > T(0)) {
-            T mag = (T)I.gamma_t * vt;
-            if (mag > (T)I.mu * load) mag = (T)I.mu * load;
+            T mag = bp.gamma_t * vt;
+            if (mag > bp.mu * load) mag = bp.mu * load;
             f[0] -= mag * vx / vt;
             f[1] -= mag * vy / vt;
         }
     }
     f[2] += fw;
-    // ---- reaction of the drag onto the fluid, one stencil node per lane ----
-    if (corner) {
-        if (flagged) {
-            T* fe = (T*)I.fext + 3 * idl;
-            const T c = -(T)dt * wdl;
-            for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
-        } else {
-            err |= ERR_BEAD;
+    // ---- reaction of the drag onto the fluid, over the lanes' stencil corners ----
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        if (lane + k * L < 8) {
+            if (flagged[k]) {
+                T* fe = (T*)I.fext + 3 * idl[k];
+                const T c = -bp.dt * wdl[k];
+                for (int d = 0; d < 3; ++d) atomicAdd(fe + d, c * drag[d]);
+            } else {
+                err |= ERR_BEAD;
+            }
         }
     }
-    // ---- FP64 integration on lane 0 ----
-    if (lane == 0) {
-        double v[3];
-        for (int d = 0; d < 3; ++d) {
-            I.bF[3 * a + d] = (double)f[d];
-            v[d] = vh[d] + hk * (double)f[d];
-        }
+    // ---- FP64 integration, component d on lane d ----
+    double disp2 = 0.0;
+    if (lane < 3) {
+        const int d = lane;
+        const double fd = (double)(d == 0 ? f[0] : (d == 1 ? f[1] : f[2]));
+        const double vhd = d == 0 ? vh[0] : (d == 1 ? vh[1] : vh[2]);
+        const double Pd = d == 0 ? P[0] : (d == 1 ? P[1] : P[2]);
+        I.bF[3 * a + d] = fd;
+        const double v = vhd + hk * fd;
         if (!last) {
-            double X[3];
-            for (int d = 0; d < 3; ++d) {
-                const double v2 = v[d] + hk * (double)f[d];
-                I.bvh[3 * a + d] = v2;
-                X[d] = P[d] + dt * v2;
-            }
-            X[0] = wrap1(X[0], I.nx);
-            X[1] = wrap1(X[1], I.ny);
-            if (!(X[2] > -0.5 && X[2] < I.nz - 0.5)) err |= ERR_BEAD;
-            for (int d = 0; d < 3; ++d) nxt[3 * a + d] = X[d];
+            const double v2 = v + hk * fd;
+            I.bvh[3 * a + d] = v2;
+            double X = Pd + dt * v2;
+            if (d == 0)
+                X = wrap1(X, I.nx);
+            else if (d == 1)
+                X = wrap1(X, I.ny);
+            else if (!(X > -0.5 && X < I.nz - 0.5))
+                err |= ERR_BEAD;
+            nxt[3 * a + d] = X;
         } else {
-            for (int d = 0; d < 3; ++d) {
-                I.bv[3 * a + d] = v[d];
-                if (cur != I.bx) I.bx[3 * a + d] = P[d];
-            }
-            const double dx = min_image(P[0] - I.bx0[3 * a], I.nx),
-                         dy = min_image(P[1] - I.bx0[3 * a + 1], I.ny), dz = P[2] - I.bx0[3 * a + 2];
-            if (dx * dx + dy * dy + dz * dz > 0.25) err |= ERR_BEAD;
+            I.bv[3 * a + d] = v;
+            if (cur != I.bx) I.bx[3 * a + d] = Pd;
+            double dd = Pd - I.bx0[3 * a + d];
+            if (d == 0)
+                dd = min_image(dd, I.nx);
+            else if (d == 1)
+                dd = min_image(dd, I.ny);
+            disp2 = dd * dd;
         }
+    }
+    if (last) {
+        // a bead that moved more than half a cell since its neighbour list was built
+        disp2 = group_sum<L>(disp2, gmask);
+        if (lane == 0 && disp2 > 0.25) err |= ERR_BEAD;
     }
     if (err) atomicOr(I.err, err);
 }

@@ -24,7 +24,9 @@ namespace {
 
 // Tilings of the fused kernel the autotuner chooses from: columns of tx-by-ty
 // nodes, then a z-chunk per block (chunk 0 means "split until the whole batch
-// fills the GPU"; chunks above nz take the whole column), and the register
+// fills the GPU"; chunks above nz take the whole column; chunk -1 means whole
+// columns in full waves of resident blocks, then the rest of the columns in
+// chunks short enough to fill the last waves, see make_tiles), and the register
 // budget as resident blocks per SM (128 registers a thread: 4 blocks of 32x4,
 // 2 of 32x8; a 96-register form of 32x4 at 5 blocks per SM measured 5-40 %
 // slower on every workload, a spill-free 168-register form at 3 blocks 6-16 %
@@ -39,7 +41,7 @@ struct Shape {
 const Shape SHAPES[] = {{32, 8, 0, 2, 0}, {32, 8, 16, 2, 0}, {32, 8, 32, 2, 0}, {32, 8, 64, 2, 0},
                         {32, 4, 0, 4, 0}, {32, 4, 16, 4, 0}, {32, 4, 32, 4, 0}, {32, 4, 64, 4, 0},
                         {32, 8, 0, 2, 1}, {32, 8, 32, 2, 1}, {32, 4, 0, 4, 1}, {32, 4, 32, 4, 1},
-                        {32, 4, 64, 4, 1}};
+                        {32, 4, 64, 4, 1}, {32, 4, -1, 4, 0}, {32, 8, -1, 2, 0}};
 constexpr int NSHAPES = sizeof(SHAPES) / sizeof(SHAPES[0]);
 constexpr int MAX_NBR = 128;
 constexpr size_t STAGE_BYTES = size_t(64) << 20;
@@ -114,10 +116,81 @@ std::vector<std::pair<int, int>> z_chunks(int nz, int ch) {
     return zr;
 }
 
+// Whole columns in full waves, then chunks (chunk -1).  With S = 148 x minb resident
+// blocks, a whole wave of column blocks costs nz planes plus the start of a block
+// (its first C and normal planes and the flush of its boundary planes, about
+// START_PLANES planes of work), and the blocks that do not fill a wave are better
+// cut into chunks, so that the last waves end together.  The head (the first
+// `head` columns, in column order, marching up in step) and the tail chunk are
+// chosen by that cost model; the tail goes out chunk by chunk, the columns of a
+// chunk in order, so that neighbouring blocks still march in step.
+constexpr int RESIDENT_SMS = 148;
+constexpr double START_PLANES = 4.0;
+struct MixedPlan {
+    long long head = 0;  // columns taken whole
+    int tail_chunk = 0;  // planes per block of the other columns (0: none left)
+};
+MixedPlan mixed_plan(const lbm_config* cfgs, int n, const Shape& sh) {
+    const long long cols = column_tiles(cfgs, n, sh);
+    const long long S = (long long)RESIDENT_SMS * sh.minb;
+    int nzmax = 2;
+    for (int k = 0; k < n; ++k) nzmax = std::max(nzmax, std::min(cfgs[k].nz, MAX_CHUNK));
+    MixedPlan best;
+    double bt = 1e300;
+    for (long long w = cols / S; w >= 0 && w >= cols / S - 1; --w) {
+        const long long head = w * S, rest = cols - head;
+        const int chunks[] = {0, 8, 12, 16, 24, 32, 48, 64};
+        for (int c : chunks) {
+            if ((c == 0) != (rest == 0) || c >= nzmax) continue;
+            double t = (double)w * (nzmax + START_PLANES);
+            if (rest > 0) {
+                const long long per = (nzmax + c - 1) / c;
+                t += (double)((rest * per + S - 1) / S) * (c + START_PLANES);
+            }
+            if (t < bt) {
+                bt = t;
+                best.head = head;
+                best.tail_chunk = c;
+            }
+        }
+    }
+    return best;
+}
+
 // the tile table of a tiling: one column piece per block
 std::vector<TileDesc> make_tiles(const lbm_config* cfgs, int n, const Shape& sh) {
     const long long cols_all = column_tiles(cfgs, n, sh);
     std::vector<TileDesc> t;
+    if (sh.chunk < 0) {
+        const MixedPlan mp = mixed_plan(cfgs, n, sh);
+        if (mp.head > 0 || mp.tail_chunk > 0) {
+            struct Col {
+                int inst, x0, y0;
+            };
+            std::vector<Col> col;
+            for (int k = 0; k < n; ++k)
+                for (int y0 = 0; y0 < cfgs[k].ny; y0 += sh.ty)
+                    for (int x0 = 0; x0 < cfgs[k].nx; x0 += sh.tx) col.push_back(Col{k, x0, y0});
+            for (long long j = 0; j < mp.head; ++j)
+                for (auto& r : z_chunks(cfgs[col[j].inst].nz, std::min(cfgs[col[j].inst].nz, MAX_CHUNK)))
+                    t.push_back(TileDesc{col[j].inst, col[j].x0, col[j].y0, r.first, r.second, 0, 0, 0});
+            if (mp.tail_chunk > 0) {
+                // chunk index outer, so that the blocks of one chunk level go out together
+                int most = 0;
+                std::vector<std::vector<std::pair<int, int>>> zr(col.size());
+                for (size_t j = (size_t)mp.head; j < col.size(); ++j) {
+                    zr[j] = z_chunks(cfgs[col[j].inst].nz, mp.tail_chunk);
+                    most = std::max(most, (int)zr[j].size());
+                }
+                for (int q = 0; q < most; ++q)
+                    for (size_t j = (size_t)mp.head; j < col.size(); ++j)
+                        if (q < (int)zr[j].size())
+                            t.push_back(TileDesc{col[j].inst, col[j].x0, col[j].y0, zr[j][q].first,
+                                                 zr[j][q].second, 0, 0, 0});
+            }
+            return t;
+        }
+    }
     for (int k = 0; k < n; ++k) {
         const lbm_config& c = cfgs[k];
         for (auto& r : z_chunks(c.nz, chunk_z(c, sh, cols_all)))
@@ -407,16 +480,17 @@ lbm_status launch_bead_step(lbm_handle* h, cudaEvent_t before, cudaEvent_t after
     const int S_ = h->cfg[0].substeps;
     // blocks of 64 threads, so that the FP64 integration and the stencils of a few
     // hundred beads spread over many SMs; sixteen lanes per bead up to 2048 beads in
-    // the whole batch (measured faster at 800), eight beyond (more beads per warp:
-    // faster at 16,000 in one lattice and at 18,000 over 64)
+    // the whole batch (measured faster at 800), four beyond (more beads per warp share
+    // the per-bead FP64 steps, which the narrow FP64 pipe makes the limit at 16,000
+    // beads in one lattice and at 18,000 over 64)
     int total_nb = 0;
     for (auto& I : h->L.inst) total_nb += I.nb;
     if (total_nb <= 2048) {
         const dim3 g((h->max_nb * 16 + 63) / 64, n);
         for (int s = 1; s <= S_; ++s) k_bead_force<T, 16><<<g, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
     } else {
-        const dim3 g((h->max_nb * 8 + 63) / 64, n);
-        for (int s = 1; s <= S_; ++s) k_bead_force<T, 8><<<g, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
+        const dim3 g((h->max_nb * 4 + 63) / 64, n);
+        for (int s = 1; s <= S_; ++s) k_bead_force<T, 4><<<g, 64, 0, h->stream>>>(h->L.d_inst, h->L.glob, s);
     }
     CK(cudaGetLastError());
     CK(cudaStreamWaitEvent(h->stream, h->ev_side, 0));  // column heights before the fused kernel
@@ -880,6 +954,19 @@ lbm_status lbm_create(const lbm_config* cfgs, int n, void* dev_ws, size_t ws_byt
         I.mass = c.bead_mass;
         I.dt_sub = 1.0 / c.substeps;
         I.hk_sub = 0.5 * I.dt_sub / c.bead_mass;
+        I.f_ks = (float)I.ks;
+        I.f_Rm2 = (float)(I.Rm * I.Rm);
+        I.f_d0 = (float)I.d0;
+        I.f_eps_wca = (float)I.eps_wca;
+        I.f_kb = (float)I.kb;
+        I.f_eps_coh = (float)I.eps_coh;
+        I.f_eps_s = (float)I.eps_s;
+        I.f_rc = (float)I.rc;
+        I.f_gamma = (float)I.gamma;
+        I.f_xi = (float)I.xi;
+        I.f_mu = (float)I.mu;
+        I.f_gamma_t = (float)I.gamma_t;
+        I.f_dt_sub = (float)I.dt_sub;
         I.rlist = rlist_of(c);
         I.rcon = c.rcon;
         I.x_src = c.x_src;

@@ -344,6 +344,10 @@ struct InstDev {
     int* nnbr;
     double ks, Rm, d0, eps_wca, kb, eps_coh, eps_s, rc, gamma, xi, mu, gamma_t, mass, rlist;
     double dt_sub, hk_sub;       // sub-step 1/substeps and half kick dt/(2 m)
+    // FP32 roundings of the force parameters (Rm as Rm^2), made on the host: the FP32
+    // force path then converts nothing from FP64 per thread
+    float f_ks, f_Rm2, f_d0, f_eps_wca, f_kb, f_eps_coh, f_eps_s, f_rc, f_gamma, f_xi, f_mu, f_gamma_t;
+    float f_dt_sub, f_pad[3];
     // cell list of large instances (cells at least rlist wide)
     int cgx, cgy, cgz, pad2;
     int* ccount;                 // beads filed per cell this step

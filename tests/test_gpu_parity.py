@@ -356,7 +356,8 @@ def test_full_size_c2_step_in_bench_configuration(lbm, oracle):
 
 def test_full_size_c4_batch_step_on_sampled_lattices(lbm, oracle):
     """The 64-lattice FP16 batch (26.7 M nodes, 64..192 x 64 x 48) as the benchmark runs it: one
-    step of the whole batch under two tilings (whole columns, 16-plane chunks); three sampled
+    step of the whole batch under four tilings (whole columns, 16-plane chunks, and the two mixed
+    tilings: whole columns in full waves, then the remaining columns in short chunks); three sampled
     lattices (smallest, a middle one with cohesion, largest) start from oracle droplets with wires
     placed by the test and are compared with the FP64 oracle, every population."""
     from paper_2607_06794_b300 import workloads
@@ -380,8 +381,13 @@ def test_full_size_c4_batch_step_on_sampled_lattices(lbm, oracle):
         acc = oracle.Acc()
         oracle.step(p, fR, fB, cot, acc, ob)
         refs[k] = (fR, fB, ob.X.copy(), acc)
-    # 32x4 columns: the automatic chunk (whole 48-plane columns over this batch), 16-plane chunks
-    for t in (4, 5):
+    # 32x4 columns: the automatic chunk (whole 48-plane columns over this batch), 16-plane chunks;
+    # the mixed tilings on 32x4 and 32x8 columns
+    big = [lbm.Config(512, 256, 128)]  # 128 planes divide into every fixed chunk
+    mixed = [k for k in range(lbm.tiling_count())
+             if len(np.unique(np.diff(lbm.tiling_table(big, k)[:, 3:5], axis=1))) > 1]
+    assert len(mixed) == 2
+    for t in [4, 5] + mixed:
         sim = lbm.Simulation(wl.cfgs)
         for k in range(len(wl.cfgs)):
             sim.set_substrate_pattern(k, wl.thetas[k])
@@ -425,6 +431,36 @@ def test_large_bead_instance_uses_cell_list_and_matches_oracle(lbm, oracle):
     assert np.allclose(sim.read(0, "bead_x"), ob.X, atol=1e-11)
     assert np.allclose(sim.read(0, "bead_f"), ob.F, atol=1e-11)
     assert pop_err(sim.read(0, "populations"), fR, fB) < 1e-11
+
+
+def test_many_beads_in_a_batch_take_four_lanes_per_bead_and_match_oracle(lbm, oracle):
+    """Above 2048 beads in the batch the sub-steps run four lanes per bead (two stencil
+    corners per lane, one integrated component per lane): two copies of the 1080-bead
+    instance, each compared with the FP64 oracle."""
+    cfg = droplet_cfg(lbm, nx=96, ny=64, nz=24, prec="fp64", max_beads=1400, eps_coh=0.006, xi=0.02,
+                      a=40, b=26, c=16, eps_s=0.01)
+    p, fR, fB, cot = oracle_state(oracle, cfg, 2)
+    lo = [cfg.cx - 34, cfg.cy - 20, 0.6]
+    hi = [cfg.cx + 34, cfg.cy + 20, 13.0]
+    cen, dirs = inputs.random_filaments(32, 270, 4, cfg.d0, lo, hi, min_dist=2.05)
+    assert len(cen) == 270
+    fil, pos, X = inputs.straight_filaments(cen, dirs, 4, cfg.d0)
+    assert X[:, 2].min() < 1.0  # some beads feel the substrate (adhesion, friction)
+    sim = lbm.Simulation([cfg, cfg])
+    for k in range(2):
+        sim.write(k, "populations", np.stack([fR, fB]))
+        sim.add_nanowires(k, 270, 8.0, cen, dirs)
+    ob = oracle.Beads(fil, pos, sim_free_positions(cen, dirs, 4, cfg))
+    acc = oracle.Acc()
+    for _ in range(2):
+        oracle.step(p, fR, fB, cot, acc, ob)
+    sim.step(2)
+    sim.sync()
+    for k in range(2):
+        assert np.allclose(sim.read(k, "bead_x"), ob.X, atol=1e-11), k
+        assert np.allclose(sim.read(k, "bead_v"), ob.V, atol=1e-11), k
+        assert np.allclose(sim.read(k, "bead_f"), ob.F, atol=1e-11), k
+        assert pop_err(sim.read(k, "populations"), fR, fB) < 1e-11, k
 
 
 def test_checkpoint_restore_with_beads_continues_the_run(lbm, oracle):

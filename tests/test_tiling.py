@@ -62,6 +62,33 @@ def test_automatic_chunk_counts_the_columns_of_the_whole_batch():
     assert np.all(tm[:, 4] - tm[:, 3] == 48)
 
 
+def test_mixed_tilings_take_whole_columns_in_full_waves_then_short_chunks():
+    # 512x256x128: 1024 columns of 32x4 (592 resident blocks of 128 threads on 148 SMs)
+    # or 512 of 32x8 (296 of 256 threads); the mixed candidates take one full wave of whole
+    # columns first, then cut the other columns into equal chunks, level by level
+    cfgs = [P.Config(512, 256, 128)]
+    mixed = 0
+    for k in range(P.tiling_count()):
+        tab = P.tiling_table(cfgs, k)
+        lens = tab[:, 4] - tab[:, 3]
+        if len(np.unique(lens)) < 2:
+            continue
+        mixed += 1
+        wave = 148 * (16 // int(tab[:, 6].max()))  # 16 warps of 128 registers per SM
+        whole = int(np.sum(lens == 128))
+        assert whole > 0 and whole % wave == 0, k
+        assert np.all(lens[:whole] == 128), k  # the whole columns go out first
+        tail = tab[whole:]
+        assert len(np.unique(tail[:, 4] - tail[:, 3])) == 1, k
+        assert np.all(np.diff(tail[:, 3]) >= 0), k  # chunk level by level
+        assert len(tail) / wave > 0.8 * np.ceil(len(tail) / wave), k  # the last wave is nearly full
+        cover = np.zeros((128, 256, 512), np.int8)
+        for inst, x0, y0, z0, z1, w, h in tab.tolist():
+            cover[z0:z1, y0:y0 + h, x0:x0 + w] += 1
+        assert cover.min() == 1 and cover.max() == 1, k
+    assert mixed >= 2
+
+
 def test_bad_arguments_are_rejected():
     with pytest.raises(RuntimeError):
         P.tiling_table(batch("c2"), P.tiling_count())
