@@ -234,8 +234,9 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     using T = typename S::T;
     using E = typename S::E;
     const InstDev& I = *Ip;
+    using V4 = typename Vec4<T>::type;
     __shared__ T sC[12][12][12];
-    __shared__ T sN[10][10][10][3];
+    __shared__ V4 sN[10][10][10];  // unit normals (w unused): one 16/32-byte access each
     const long long step = __ldcg(&glob->step);
     const T* rho = (const T*)I.rho[step % 3];
     const int nx = I.nx, ny = I.ny, nz = I.nz;
@@ -288,7 +289,6 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     for (int s = tid; s < 1000; s += 512) {
         const int lx = s % 10, ly = (s / 10) % 10, lz = s / 100;
         const int z = Z0 - 1 + lz;
-        T* nn = sN[lz][ly][lx];
         if (z < 0 || z >= nz) continue;
         T gx = 0, gy = 0, gz = 0;
 #pragma unroll
@@ -302,24 +302,26 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
         gx *= T(3);
         gy *= T(3);
         gz *= T(3);
-        const T g = sqrt(gx * gx + gy * gy + gz * gz);
-        if (g > T(1e-8)) {
-            nn[0] = gx / g;
-            nn[1] = gy / g;
-            nn[2] = gz / g;
+        const T g2 = gx * gx + gy * gy + gz * gz;
+        V4 nn;
+        if (g2 > T(1e-16)) {
+            const T ig = inv_norm<T>(g2);
+            nn.x = gx * ig;
+            nn.y = gy * ig;
+            nn.z = gz * ig;
         } else {
-            nn[0] = nn[1] = nn[2] = T(0);
+            nn.x = nn.y = nn.z = T(0);
         }
+        nn.w = T(0);
+        sN[lz][ly][lx] = nn;
     }
     __syncthreads();
     // normals outside the fluid copy the nearest fluid plane
     for (int s = tid; s < 100; s += 512) {
         const int lx = s % 10, ly = s / 10;
-        if (Z0 - 1 < 0)
-            for (int d = 0; d < 3; ++d) sN[0][ly][lx][d] = sN[1][ly][lx][d];
+        if (Z0 - 1 < 0) sN[0][ly][lx] = sN[1][ly][lx];
         for (int lz = 0; lz < 10; ++lz)
-            if (Z0 - 1 + lz == nz)
-                for (int d = 0; d < 3; ++d) sN[lz][ly][lx][d] = sN[lz - 1][ly][lx][d];
+            if (Z0 - 1 + lz == nz) sN[lz][ly][lx] = sN[lz - 1][ly][lx];
     }
     __syncthreads();
     const int lx = tid % 8, ly = (tid / 8) % 8, lz = tid / 64;
@@ -345,8 +347,12 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
     gz *= T(3);
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const T* nn = sN[lz + 1 + cz(i)][ly + 1 + cy(i)][lx + 1 + cx(i)];
-        kap += (T)wq(i) * (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]);
+        const V4 nn = sN[lz + 1 + cz(i)][ly + 1 + cy(i)][lx + 1 + cx(i)];
+        T d = 0;
+        if (cx(i) != 0) d += cx(i) * nn.x;
+        if (cy(i) != 0) d += cy(i) * nn.y;
+        if (cz(i) != 0) d += cz(i) * nn.z;
+        kap += (T)wq(i) * d;
     }
     kap *= T(-3);
     const T hs = T(0.5) * (T)I.sigma;
@@ -364,12 +370,12 @@ __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobal
         jy += cy(i) * F;
         jz += cz(i) * F;
     }
-    const T rr = rR + rB;
+    const T irr = T(1) / (rR + rB);
     T* u = (T*)I.ust + 3 * node;
     T* g = (T*)I.gcol + 3 * node;
-    u[0] = (jx + T(0.5) * (hs * kap * gx + (T)I.body[0])) / rr;
-    u[1] = (jy + T(0.5) * (hs * kap * gy + (T)I.body[1])) / rr;
-    u[2] = (jz + T(0.5) * (hs * kap * gz + (T)I.body[2])) / rr;
+    u[0] = (jx + T(0.5) * (hs * kap * gx + (T)I.body[0])) * irr;
+    u[1] = (jy + T(0.5) * (hs * kap * gy + (T)I.body[1])) * irr;
+    u[2] = (jz + T(0.5) * (hs * kap * gz + (T)I.body[2])) * irr;
     g[0] = gx;
     g[1] = gy;
     g[2] = gz;
