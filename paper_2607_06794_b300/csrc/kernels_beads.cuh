@@ -70,32 +70,45 @@ __device__ __forceinline__ T pair_dUdr(const BeadPar<T>& bp, bool same, int sep,
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 __device__ __forceinline__ double wrap1(double a, int n) { return a < 0.0 ? a + n : (a >= n ? a - n : a); }
 
-// Corner c (bit 0: x, bit 1: y, bit 2: z) of the trilinear stencil around a
-// position (z clamped into the fluid): node index, weight and 8^3 coupling tile.
-// Positions are kept inside the periodic box by the integrator; a non-finite
-// position (already an error) is mapped to the origin so that no index is
-// ever formed from it.
-// W = double computes the weight in FP64; W = float takes the cell and its
-// fraction in FP64 and the weight in FP32.
+// The trilinear stencil around a position (z clamped into the fluid): its lower
+// corner cell and the fractions.  Positions are kept inside the periodic box by the
+// integrator; a non-finite position (already an error) is mapped to the origin so
+// that no index is ever formed from it.  W = double computes the fractions in FP64;
+// W = float takes the cell and its fraction in FP64 and rounds the fraction to FP32.
 template <typename W>
-__device__ __forceinline__ void stencil_corner(const InstDev& I, const double* X, int c, long long& id, W& w,
-                                               int& tile) {
+struct StencilCell {
+    int x0, y0, z0;
+    W fx, fy, fz;
+};
+template <typename W>
+__device__ __forceinline__ StencilCell<W> stencil_cell(const InstDev& I, const double* X) {
     double px = X[0], py = X[1], pz = X[2];
     if (!(isfinite(px) && isfinite(py) && isfinite(pz))) px = py = pz = 0.0;
     px = wrap1(px, I.nx);
     py = wrap1(py, I.ny);
     pz = pz < 0.0 ? 0.0 : (pz > I.nz - 1 ? (double)(I.nz - 1) : pz);
-    const int x0 = min(max((int)floor(px), 0), I.nx - 1), y0 = min(max((int)floor(py), 0), I.ny - 1);
-    int z0 = (int)floor(pz);
-    if (I.nz >= 2 && z0 > I.nz - 2) z0 = I.nz - 2;
-    const W fx = (W)(px - x0), fy = (W)(py - y0), fz = (W)(pz - z0);
-    const int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
-    const int xx = wrap1(x0 + a, I.nx), yy = wrap1(y0 + b, I.ny), zz = (e && I.nz >= 2) ? z0 + 1 : z0;
-    id = ((long long)zz * I.ny + yy) * I.nx + xx;
-    w = (a ? fx : W(1) - fx) * (b ? fy : W(1) - fy) * (e ? fz : W(1) - fz);
-    tile = ((zz >> 3) * I.t8y + (yy >> 3)) * I.t8x + (xx >> 3);
+    StencilCell<W> sc;
+    sc.x0 = min(max((int)floor(px), 0), I.nx - 1);
+    sc.y0 = min(max((int)floor(py), 0), I.ny - 1);
+    sc.z0 = (int)floor(pz);
+    if (I.nz >= 2 && sc.z0 > I.nz - 2) sc.z0 = I.nz - 2;
+    sc.fx = (W)(px - sc.x0);
+    sc.fy = (W)(py - sc.y0);
+    sc.fz = (W)(pz - sc.z0);
+    return sc;
 }
 
+// Corner c (bit 0: x, bit 1: y, bit 2: z) of a stencil: node index, weight and
+// 8^3 coupling tile.
+template <typename W>
+__device__ __forceinline__ void stencil_corner(const InstDev& I, const StencilCell<W>& sc, int c, long long& id,
+                                               W& w, int& tile) {
+    const int a = c & 1, b = (c >> 1) & 1, e = c >> 2;
+    const int xx = wrap1(sc.x0 + a, I.nx), yy = wrap1(sc.y0 + b, I.ny), zz = (e && I.nz >= 2) ? sc.z0 + 1 : sc.z0;
+    id = ((long long)zz * I.ny + yy) * I.nx + xx;
+    w = (a ? sc.fx : W(1) - sc.fx) * (b ? sc.fy : W(1) - sc.fy) * (e ? sc.fz : W(1) - sc.fz);
+    tile = ((zz >> 3) * I.t8y + (yy >> 3)) * I.t8x + (xx >> 3);
+}
 // cell of a (finite, wrapped) position; cells are at least rlist wide
 __device__ __forceinline__ int cell_of(const InstDev& I, float x, float y, float z) {
     int cx_ = (int)(x * I.cgx / I.nx), cy_ = (int)(y * I.cgy / I.ny), cz_ = (int)((z + 0.5f) * I.cgz / I.nz);
@@ -213,9 +226,12 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts, const StepGlobal
 template <class S, bool EP>
 __device__ void bead_field_tile(const InstDev* __restrict__ Ip, const StepGlobals* __restrict__ glob, int t);
 
-// EP: the populations are stored in place (esoteric pull), else in two buffers
+// EP: the populations are stored in place (esoteric pull), else in two buffers.
+// Three blocks per SM (40 registers a thread): the pass waits on global loads twice
+// per tile (colour block, pulls), and a third resident block hides more of that than
+// the few spilled registers cost (four blocks spill ~250 bytes a thread)
 template <class S, bool EP>
-__global__ void __launch_bounds__(512) k_bead_field(const InstDev* __restrict__ insts,
+__global__ void __launch_bounds__(512, 3) k_bead_field(const InstDev* __restrict__ insts,
                                                     const StepGlobals* __restrict__ glob) {
     using T = typename S::T;
     using E = typename S::E;
@@ -506,6 +522,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     long long idl[CPL];
     T wdl[CPL], uc[CPL][3], gcc[CPL][3];
     unsigned flagged[CPL];
+    const StencilCell<T> sc = stencil_cell<T>(I, P);  // once per lane, whatever its corners
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         const int c = lane + k * L;
@@ -515,7 +532,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
         for (int d = 0; d < 3; ++d) uc[k][d] = gcc[k][d] = 0;
         if (c < 8) {
             int tl = 0;
-            stencil_corner(I, P, c, idl[k], wdl[k], tl);
+            stencil_corner(I, sc, c, idl[k], wdl[k], tl);
             const T* ust = (const T*)I.ust + 3 * idl[k];
             const T* gcl = (const T*)I.gcol + 3 * idl[k];
             for (int d = 0; d < 3; ++d) {
@@ -580,8 +597,9 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
         u[d] = group_sum<L>(su, gmask);
         gc[d] = group_sum<L>(sg, gmask);
     }
+    const T vt3[3] = {(T)vh[0], (T)vh[1], (T)vh[2]};
     T drag[3];
-    for (int d = 0; d < 3; ++d) drag[d] = bp.gamma * (u[d] - (T)vh[d]);
+    for (int d = 0; d < 3; ++d) drag[d] = bp.gamma * (u[d] - vt3[d]);
     T f[3] = {fx + drag[0] + bp.xi * gc[0], fy + drag[1] + bp.xi * gc[1], fz + drag[2] + bp.xi * gc[2]};
     // ---- substrate adhesion (LJ at the image distance) and load-dependent friction ----
     const T rw = T(2) * ((T)P[2] + T(0.5));
@@ -589,7 +607,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     if (bp.has_s && rw < bp.rc && rw > T(0)) fw = T(-2) * bp.eps_s * lj_shape_dr<T>(bp.d0, rw);
     if (bp.has_s && rw < bp.rc) {
         const T load = (f[2] < T(0) ? -f[2] : T(0)) + (fw < T(0) ? -fw : T(0));
-        const T vx = (T)vh[0], vy = (T)vh[1];
+        const T vx = vt3[0], vy = vt3[1];
         const T vt = sqrt(vx * vx + vy * vy);
         if (vt > T(0)) {
             T mag = bp.gamma_t * vt;

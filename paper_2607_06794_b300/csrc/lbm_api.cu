@@ -472,7 +472,7 @@ lbm_status launch_bead_step(lbm_handle* h, cudaEvent_t before, cudaEvent_t after
     CK(cudaEventRecord(h->ev_side, h->side));
     int maxt = 0;
     for (auto& I : h->L.inst) maxt = std::max(maxt, I.ntile);
-    const dim3 fgrid(std::min(maxt, 2 * 148), n);
+    const dim3 fgrid(std::min(maxt, 3 * 148), n);  // every resident block of k_bead_field
     if (h->inplace)
         k_bead_field<S, true><<<fgrid, 512, 0, h->stream>>>(h->L.d_inst, h->L.glob);
     else
