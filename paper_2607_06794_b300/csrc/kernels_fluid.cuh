@@ -141,10 +141,20 @@ __device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned 
 // try_wait polls before a wait is declared lost
 constexpr int MBAR_POLLS = 1 << 16;
 
+// Colour C = (rho_R - rho_B)/(rho_R + rho_B) of component densities a, b.  FP64
+// divides.  FP32 takes the fast reciprocal, through the smaller fraction:
+// C = 2 min(a, b)/(a + b) - 1 (or 1 - that), so that a pure or nearly pure phase
+// (the smaller density below half an ulp of the sum) comes out exactly -1 or +1, as
+// correctly rounded division gives, where a quotient of two equal numbers from the
+// fast reciprocal may miss 1 by an ulp.  Uniform pure regions then have exactly zero
+// colour gradient.
 template <typename T>
-__device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+__device__ __forceinline__ T colour_q(T a, T b) { return (a - b) / (a + b); }
 template <>
-__device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float colour_q<float>(float a, float b) {
+    const float t = __fdividef(2.0f * fminf(a, b), a + b);
+    return a < b ? t - 1.0f : 1.0f - t;
+}
 
 template <typename T>
 __device__ __forceinline__ T inv_norm(T g2);
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(HCOL_X * HCOL_Z) k_column_height(const InstDev
     if (c < (int)nxy)
         for (int z = threadIdx.y; z < I.nz; z += HCOL_Z) {
             const T a = rho[(unsigned)z * nxy + c], b = rho[N + (unsigned)z * nxy + c];
-            h += (T(1) + qdiv<T>(a - b, a + b)) / T(2);
+            h += (T(1) + colour_q<T>(a, b)) / T(2);
         }
     part[threadIdx.y][threadIdx.x] = h;
     __syncthreads();
@@ -289,10 +299,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const T J0 = (T)Ig.J0, Kk = (T)Ig.K, inv_h0 = evap_on ? (T)(1.0 / h0) : T(0);
 
     auto ring = [](int q) { return ((q % 3) + 3) % 3; };
-    auto colour = [&](unsigned n) {
-        const T a = rho_r[n], b = rho_r[N + n];
-        return qdiv<T>(a - b, a + b);
-    };
+    auto colour = [&](unsigned n) { return colour_q<T>(rho_r[n], rho_r[N + n]); };
     // wetting ghost colour below z = 0 (flat-wall geometric form, D2Q9 weights)
     auto ghost = [&](int gx, int gy) {
         T ax = 0, ay = 0;
@@ -367,12 +374,19 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             }
         }
     };
-    auto commitC = [&]() {
-        if (pfp < 0 || pfp > nz) return;
+    // commit the prefetched plane; true when every slot this thread wrote is pure gas (C = -1)
+    auto commitC = [&]() -> bool {
+        if (pfp < 0 || pfp > nz) return false;
         T* ringp = &sC[ring(pfp)][0][0];
+        bool gas = true;
 #pragma unroll
         for (int k = 0; k < NPF; ++k)
-            if (pfo[k] != ~0u) ringp[tid + k * NT] = qdiv<T>(pfa[k] - pfb[k], pfa[k] + pfb[k]);
+            if (pfo[k] != ~0u) {
+                const T c = colour_q<T>(pfa[k], pfb[k]);
+                ringp[tid + k * NT] = c;
+                gas = gas && c == T(-1);
+            }
+        return gas;
     };
     // gradient and unit normal of plane q over the tile plus 1 cell: every thread
     // takes its own node, the first 2 HX1 + 2 TY threads one node of the ring around
@@ -419,9 +433,19 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         nn.w = T(0);
         return nn;
     };
-    auto computeN = [&](int q) {
+    // skip: the colour of planes q-1..q+1 is -1 over the whole ring, so every gradient and
+    // normal of plane q is exactly zero (opposite directions cancel term by term)
+    auto computeN = [&](int q, bool skip) {
         const int rq = ring(q);
-        if (q >= 0 && q < nz) {
+        if (skip) {
+            V4 zero;
+            zero.x = zero.y = zero.z = zero.w = T(0);
+            if (active) {
+                sN[rq][ty + 1][tx + 1] = zero;
+                sG[q & 1][ty][tx] = zero;
+            }
+            if (nring >= 0) (&sN[rq][0][0])[nring] = zero;
+        } else if (q >= 0 && q < nz) {
             const int rm = ring(q - 1), r0 = ring(q), rp = ring(q + 1);
             T gx, gy, gz;
             if (active) {
@@ -702,19 +726,19 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         loadC(0);
         loadC(1);
         __syncthreads();
-        computeN(0);
+        computeN(0, false);
         __syncthreads();
-        computeN(-1);
+        computeN(-1, false);
     } else {
         loadC(z0 - 2);
         loadC(z0 - 1);
         loadC(z0);
         __syncthreads();
-        computeN(z0 - 1);
+        computeN(z0 - 1, false);
         __syncthreads();
         loadC(z0 + 1);
         __syncthreads();
-        computeN(z0);
+        computeN(z0, false);
     }
     prefetchC(z0 + 2);
     if constexpr (ASYNC && !BULK) issue_pull(z0);
@@ -724,6 +748,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         if constexpr (NBUF == 2) issue_bulk(z0 + 1);
     }
 
+    // block-uniform plane flags, shifted up one plane per iteration: gasC bit k = the
+    // colour ring of plane z+2-k is -1 throughout (planes the loop committed); zeroN bit
+    // k = the normals (and core gradient) of plane z+1-k were skipped as zero
+    unsigned gasC = 0u, zeroN = 0u;
     for (int z = z0; z < z1; ++z) {
         const unsigned node = (unsigned)z * nxy + row0 + x;
         const int rz[3] = {ring(z - 1), ring(z), ring(z + 1)};  // ring slots of planes z-1, z, z+1
@@ -748,11 +776,13 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             });
         }
         flush(z - 2);
-        commitC();
+        const bool cgas = commitC();
         prefetchC(z + 3);
-        __syncthreads();
-        // ---- phase 2: normals of plane z+1 ----
-        computeN(z + 1);
+        gasC = (gasC << 1) | (__syncthreads_and(cgas) ? 1u : 0u);
+        // ---- phase 2: normals of plane z+1 (zero without computing where planes z..z+2 are pure gas) ----
+        const bool skipN = (gasC & 7u) == 7u;
+        computeN(z + 1, skipN);
+        zeroN = (zeroN << 1) | (skipN ? 1u : 0u);
         __syncthreads();
         // ---- phase 3: decode, collide, recolour, evaporate, store, push ----
         T ac1[3][2] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};  // shares of plane z+1
@@ -821,15 +851,17 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                 });
             }
             T kap = 0;
-            static_for<1, 19>([&](auto I_) {
-                constexpr int i = decltype(I_)::value;
-                const V4 nn = sN[rz[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
-                T d = 0;
-                if constexpr (cx(i) != 0) d += cx(i) * nn.x;
-                if constexpr (cy(i) != 0) d += cy(i) * nn.y;
-                if constexpr (cz(i) != 0) d += cz(i) * nn.z;
-                kap += (T)wq(i) * d;
-            });
+            if ((zeroN & 7u) != 7u) {  // else every normal of planes z-1..z+1 is zero
+                static_for<1, 19>([&](auto I_) {
+                    constexpr int i = decltype(I_)::value;
+                    const V4 nn = sN[rz[cz(i) + 1]][ty + 1 + cy(i)][tx + 1 + cx(i)];
+                    T d = 0;
+                    if constexpr (cx(i) != 0) d += cx(i) * nn.x;
+                    if constexpr (cy(i) != 0) d += cy(i) * nn.y;
+                    if constexpr (cz(i) != 0) d += cz(i) * nn.z;
+                    kap += (T)wq(i) * d;
+                });
+            }
             kap *= T(-3);
             const V4 G = sG[z & 1][ty][tx];
             const T Gx = G.x, Gy = G.y, Gz = G.z;
