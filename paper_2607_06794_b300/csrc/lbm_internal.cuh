@@ -98,6 +98,12 @@ struct StoreF64 {
                                                     T rho0, T r, T b, T& rq, T& bq, unsigned) {
         store(p, cs, k, w, rho0, r, b, rq, bq);
     }
+    // an element without the red component (f^R = 0): what store gives for r = 0
+    static __device__ __forceinline__ void store_gas(E* __restrict__ p, unsigned cs, unsigned k, T w,
+                                                     T rho0, T b) {
+        p[k] = E(0);
+        p[cs + k] = b;
+    }
     static __host__ __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                            double& r, double& b) {
         r = p[k];
@@ -138,6 +144,12 @@ struct StoreF32 {
     static __device__ __forceinline__ void store_sr(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                     T rho0, T r, T b, T& rq, T& bq, unsigned) {
         store(p, cs, k, w, rho0, r, b, rq, bq);
+    }
+    // an element without the red component (f^R = 0): what store gives for r = 0
+    static __device__ __forceinline__ void store_gas(E* __restrict__ p, unsigned cs, unsigned k, T w,
+                                                     T rho0, T b) {
+        p[k] = E(0);
+        p[cs + k] = b;
     }
     static __host__ __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                            double& r, double& b) {
@@ -281,6 +293,12 @@ struct StoreShift16 {
         ((unsigned*)p)[k] = word;
         rq = r;
         bq = b;
+    }
+    // an element without the red component (f^R = 0): what store gives for r = 0 (the
+    // liquid fraction -1/2, or 0 where the total is 0)
+    static __device__ __forceinline__ void store_gas(E* __restrict__ p, unsigned cs, unsigned k, T w,
+                                                     T rho0, T b) {
+        ((unsigned*)p)[k] = Pair16<HP, HQ>::pack(b - w * rho0, b != 0.0f ? -0.5f : 0.0f);
     }
     static __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                   double& r, double& b) {
