@@ -56,7 +56,7 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
     wires: per instance (centres, directions, beads per wire) placed identically in
     every run (None: the workload's own seeded placement).  Returns, per precision,
     the shape observables every `every` steps (and at the end) and the descriptors
-    and shape at the end."""
+    and shape at the end, of instance 0 and, under "instances", of every instance."""
     out = {}
     for prec in precs:
         wl = make(prec)
@@ -85,20 +85,26 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
             for k, pw in enumerate(wires):
                 if pw is not None:
                     sim.add_nanowires(k, len(pw[0]), pw[2] * wl.cfgs[k].d0, pw[0], pw[1])
-        rec = []
+        ninst = len(wl.cfgs)
+        rec = [[] for _ in range(ninst)]
         done = 0
         every_ = steps if not every else every
         while True:
             if done % every_ == 0 or done == steps:
-                rec.append(dict(step=done, **sim.shape(0)))
+                for k in range(ninst):
+                    rec[k].append(dict(step=done, **sim.shape(k)))
             if done >= steps:
                 break
             n = min(every_ - done % every_, steps - done)
             sim.step(n)
             done += n
         sim.sync()
-        desc = sim.descriptors(0) if any(w is not None for w in (wires or wl.wires)) else None
-        out[prec] = {"series": rec, "final": rec[-1], "descriptors": desc, "status": sim.status()}
+        placed = wires or wl.wires
+        desc = [sim.descriptors(k) if placed[k] is not None else None for k in range(ninst)]
+        # instance 0 at the top level; every instance under "instances"
+        out[prec] = {"series": rec[0], "final": rec[0][-1], "descriptors": desc[0], "status": sim.status(),
+                     "instances": [{"series": rec[k], "final": rec[k][-1], "descriptors": desc[k]}
+                                   for k in range(ninst)]}
         sim.close()
         if report is not None:
             report(prec, out[prec])

@@ -9,11 +9,16 @@ run, which the parity tests tie to the FP64 oracle.  The target is 1 % in
 volume and in contact-line extent for both formats.
 
 The deposit descriptors (S_x of Eq. (13); contact clusters and percolation of
-Sec. II.B) come from the 256x128x64 stripe droplet with 200 wires, run with
-identical wires in FP64, FP16 and BF16 until the droplet has dried.  The bead
-trajectories of a drying run are chaotic (contacts form or not by a fraction of
-a lattice unit), so the descriptors of the 16-bit runs are reported against
-FP64 with bounds on the statistics, not bit-level agreement.
+Sec. II.B) come from the 256x128x64 stripe droplet with 200 wires, four wire
+placements (seeds) run as one batch, with identical wires in FP64, FP16 and
+BF16 until the droplets have dried.  The bead trajectories of a drying run are
+chaotic (a contact forms or not by a fraction of a lattice unit, and the order
+of the floating-point atomic adds already changes the last bits from run to
+run): two FP64 runs of the same placement end 0.01-0.04 apart in S_x, and one
+placement's deposit can move by 0.1-0.2 between runs whose launch layout
+differs.  So the 16-bit descriptors are compared with FP64 as statistics over
+the four placements (the mean S_x within 0.1, the mean cluster count within
+one, the percolation verdicts), and every per-placement figure is reported.
 
 With round-to-nearest storage the sink's per-step change of the rest
 population's liquid fraction (~1e-4) is below half a unit in the last place of
@@ -108,27 +113,44 @@ def test_16bit_storage_keeps_volume_and_contact_line_within_one_percent(c1_runs,
     assert abs(ey - ey64) / ey64 < TARGET, (prec, ey, ey64)
 
 
+NSEED = 4  # wire placements of the deposit comparison, run as one batch
+
+
 @pytest.fixture(scope="module")
 def c2_deposits(lbm):
+    import dataclasses
+
     from paper_2607_06794_b300 import experiments, workloads
     from tests import inputs
 
-    c = workloads.droplet_c2("fp64").cfgs[0]
-    qmax = 1.0 - np.arctanh(0.9) * c.width / min(c.a, c.b, c.c)
-    cen, dirs = inputs.wires_in_droplet(c.seed, 200, 4, c.d0, (c.nx, c.ny, c.nz), (c.cx, c.cy, c.cz),
-                                        (c.a, c.b, c.c), qmax)
-    res = experiments.storage_comparison(workloads.droplet_c2, ("fp64", "fp16", "bf16"), STEPS_C2,
-                                         every=1000, wires=[(cen, dirs, 4)])
+    def batch(prec):
+        w = workloads.droplet_c2(prec)
+        cfgs = [dataclasses.replace(w.cfgs[0], seed=w.cfgs[0].seed + k) for k in range(NSEED)]
+        return dataclasses.replace(w, cfgs=cfgs, thetas=w.thetas * NSEED, wires=w.wires * NSEED)
+
+    wires = []
+    for c in batch("fp64").cfgs:
+        qmax = 1.0 - np.arctanh(0.9) * c.width / min(c.a, c.b, c.c)
+        cen, dirs = inputs.wires_in_droplet(c.seed, 200, 4, c.d0, (c.nx, c.ny, c.nz), (c.cx, c.cy, c.cz),
+                                            (c.a, c.b, c.c), qmax)
+        wires.append((cen, dirs, 4))
+    res = experiments.storage_comparison(batch, ("fp64", "fp16", "bf16"), STEPS_C2, every=1000, wires=wires)
     rep = {}
     for p, r in res.items():
-        d = r["descriptors"]
-        rep[p] = dict(S_x=d["S_x"], n_clusters=d["n_clusters"], percolates=d["percolates"],
-                      final_volume=r["final"]["volume"], status=r["status"],
-                      volume_series=[round(s["volume"], 2) for s in r["series"]])
+        inst = r["instances"]
+        rep[p] = dict(S_x=[i["descriptors"]["S_x"] for i in inst],
+                      n_clusters=[i["descriptors"]["n_clusters"] for i in inst],
+                      percolates=[i["descriptors"]["percolates"] for i in inst],
+                      final_volume=[i["final"]["volume"] for i in inst], status=r["status"],
+                      volume_series=[[round(s["volume"], 2) for s in i["series"]] for i in inst])
+        rep[p]["S_x_mean"] = float(np.mean(rep[p]["S_x"]))
+        rep[p]["S_x_std"] = float(np.std(rep[p]["S_x"], ddof=1))
+        rep[p]["n_clusters_mean"] = float(np.mean(rep[p]["n_clusters"]))
     for p in ("fp16", "bf16"):
-        rep[p]["S_x_err"] = rep[p]["S_x"] - rep["fp64"]["S_x"]
-        rep[p]["clusters_err"] = rep[p]["n_clusters"] - rep["fp64"]["n_clusters"]
-        rep[p]["percolation_agrees"] = rep[p]["percolates"] == rep["fp64"]["percolates"]
+        rep[p]["S_x_err_per_seed"] = [a - b for a, b in zip(rep[p]["S_x"], rep["fp64"]["S_x"])]
+        rep[p]["S_x_err_mean"] = rep[p]["S_x_mean"] - rep["fp64"]["S_x_mean"]
+        rep[p]["clusters_err_mean"] = rep[p]["n_clusters_mean"] - rep["fp64"]["n_clusters_mean"]
+        rep[p]["percolation_agrees"] = [a == b for a, b in zip(rep[p]["percolates"], rep["fp64"]["percolates"])]
     report("precision_c2_deposit", rep)
     return rep
 
@@ -137,17 +159,19 @@ def test_the_runs_reach_a_deposit(c2_deposits):
     for p in ("fp64", "fp16", "bf16"):
         r = c2_deposits[p]
         assert r["status"] == 0, p
-        assert r["final_volume"] < 0.02 * r["volume_series"][0], p  # dried
+        for v, series in zip(r["final_volume"], r["volume_series"]):
+            assert v < 0.02 * series[0], p  # dried
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_deposit_descriptors_of_16bit_storage_against_fp64(c2_deposits, prec):
     r, r64 = c2_deposits[prec], c2_deposits["fp64"]
-    # the drying time itself agrees to the 1 % volume target along the way
-    v64 = np.array(r64["volume_series"])
-    v = np.array(r["volume_series"])
-    live = v64 > 0.2 * v64[0]
-    assert np.all(np.abs(v[live] - v64[live]) <= TARGET * v64[0]), (prec, v, v64)
-    # chaotic bead trajectories: the statistics of the deposit agree
-    assert abs(r["S_x_err"]) < 0.1, r
-    assert abs(r["clusters_err"]) <= max(3, 0.25 * r64["n_clusters"]), r
+    # the drying itself agrees to the 1 % volume target along the way, placement by placement
+    for v, v64 in zip(r["volume_series"], r64["volume_series"]):
+        v, v64 = np.array(v), np.array(v64)
+        live = v64 > 0.2 * v64[0]
+        assert np.all(np.abs(v[live] - v64[live]) <= TARGET * v64[0]), (prec, v, v64)
+    # chaotic bead trajectories: the statistics of the deposits agree
+    assert abs(r["S_x_err_mean"]) < 0.1, r
+    assert abs(r["clusters_err_mean"]) <= 1.0, r
+    assert sum(r["percolation_agrees"]) >= NSEED - 1, r
