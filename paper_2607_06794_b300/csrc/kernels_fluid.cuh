@@ -912,7 +912,17 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                 if constexpr (R0) {
                     rq = T(0);
                     bq = post;
-                    S::store_gas(dst, cs, (unsigned)i * N + node, w, rho0, bq);
+                    unsigned k = (unsigned)i * N + node;
+                    if constexpr (EP && i != 0) {  // interior planes: no ghost slot
+                        if constexpr (i & 1) {
+                            const int tx_ = cx(i) == 1 ? xp : (cx(i) == -1 ? xm : x);
+                            const unsigned trow = cy(i) == 1 ? rowp : (cy(i) == -1 ? rowm : row0);
+                            k = (pa ? (unsigned)(i + 1) : (unsigned)i) * N + (unsigned)(z + cz(i)) * nxy + trow + tx_;
+                        } else {
+                            k = (pa ? (unsigned)(i - 1) : (unsigned)i) * N + node;
+                        }
+                    }
+                    S::store_gas(dst, cs, k, w, rho0, bq);
                 } else {
                     T r = phi * post;
                     if constexpr (i != 0) r += (axis ? cw_axis : cw_diag) * cG;
@@ -1010,12 +1020,12 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                     emit(std::integral_constant<int, i + 1>{}, omc * Fi[i + 1] + (A - B), -cG, RED0_);
                 });
             };
-            // interior planes of two-buffer 16-bit storage: a warp whose nodes hold no red takes
-            // the red-free form (the choice is per warp, no block vote needed), which drops the
+            // interior planes of 16-bit storage: a warp whose nodes hold no red takes the
+            // red-free form (the choice is per warp, no block vote needed), which drops the
             // division and rounding of the liquid fraction and half the push.  Measured: FP16
             // 1.014 -> 0.915 ms on the 512x256x128 lattice; FP32, which has no encode to drop,
             // ran 1-1.5 % slower with it (the second form's registers), so it keeps one form
-            if constexpr (!EDGE && !EP && S::WORDS == 1) {
+            if constexpr (!EDGE && S::WORDS == 1) {
                 if (__all_sync(lanes, rR == T(0)))
                     collide(std::true_type{});
                 else
