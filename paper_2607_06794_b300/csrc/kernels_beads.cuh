@@ -12,6 +12,19 @@ namespace lbm {
 // beads a neighbour-search cell can hold (cells are at least rlist wide)
 constexpr int CELL_CAP = 64;
 
+// a coordinate as its nearest lattice point and the FP32 offset from it; a
+// non-finite coordinate (already an error) maps to the origin
+__device__ __forceinline__ void split_pos(double x, int& K, float& r) {
+    if (!isfinite(x)) {
+        K = 0;
+        r = 0.0f;
+        return;
+    }
+    const double k = rint(x);
+    K = (int)k;
+    r = (float)(x - k);
+}
+
 // minimum image of a separation of two wrapped coordinates (|d| <= L)
 __device__ __forceinline__ double min_image(double d, int L) {
     const double h = 0.5 * L;
@@ -95,6 +108,31 @@ __device__ __forceinline__ StencilCell<W> stencil_cell(const InstDev& I, const d
     sc.fx = (W)(px - sc.x0);
     sc.fy = (W)(py - sc.y0);
     sc.fz = (W)(pz - sc.z0);
+    return sc;
+}
+
+// The same from a split position (x = K + r): floor and fraction without FP64
+// arithmetic, with the clamps of the FP64 form (z into [0, nz - 1], the cell at
+// most nz - 2; x, y into the box)
+__device__ __forceinline__ StencilCell<float> stencil_cell_split(const InstDev& I, int4 K, float4 R) {
+    StencilCell<float> sc;
+    const int fx = K.x - (R.x < 0.0f), fy = K.y - (R.y < 0.0f), fz = K.z - (R.z < 0.0f);
+    const float rx = R.x < 0.0f ? R.x + 1.0f : R.x, ry = R.y < 0.0f ? R.y + 1.0f : R.y;
+    const float rz = R.z < 0.0f ? R.z + 1.0f : R.z;
+    sc.x0 = min(max(fx, 0), I.nx - 1);
+    sc.y0 = min(max(fy, 0), I.ny - 1);
+    sc.fx = rx;
+    sc.fy = ry;
+    if (fz < 0) {
+        sc.z0 = 0;
+        sc.fz = 0.0f;
+    } else if (fz >= I.nz - 1) {
+        sc.z0 = I.nz - 2;
+        sc.fz = 1.0f;
+    } else {
+        sc.z0 = fz;
+        sc.fz = rz;
+    }
     return sc;
 }
 
@@ -183,6 +221,19 @@ __global__ void k_bead_begin(const InstDev* __restrict__ insts, const StepGlobal
         Y[1] = wrap1(Y[1], I.ny);
         if (!(Y[2] > -0.5 && Y[2] < I.nz - 0.5)) atomicOr(I.err, ERR_BEAD);
         for (int d = 0; d < 3; ++d) I.bx2[3 * a + d] = Y[d];
+    }
+    {
+        // the split form of the sub-step-1 positions, one component per lane
+        const int d = lane < 3 ? lane : 0;
+        __syncwarp();
+        const double y = I.bx2[3 * a + d];
+        if (lane < 3) {
+            int K;
+            float r;
+            split_pos(y, K, r);
+            ((int*)(I.bK[0] + a))[d] = K;
+            ((float*)(I.bR[0] + a))[d] = r;
+        }
     }
     const double zc = X[2] < -1.0 ? -1.0 : (X[2] > I.nz ? (double)I.nz : X[2]);
     const int fx = wrap_near((int)floor(X[0]), I.nx), fy = wrap_near((int)floor(X[1]), I.ny), fz = (int)floor(zc);
@@ -515,6 +566,19 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     const BeadPar<T> bp(I);
     int err = 0;
     const double P[3] = {cur[3 * a], cur[3 * a + 1], cur[3 * a + 2]};
+    // FP32 path: the split form of the current positions ([0] mirrors bx2, [1] bx)
+    constexpr bool SPLIT = sizeof(T) == 4;
+    // (selected, not indexed: a runtime index into the record would put it in local memory)
+    const int4* Kc = (s & 1) ? I.bK[0] : I.bK[1];
+    const float4* Rc = (s & 1) ? I.bR[0] : I.bR[1];
+    int4* Kn = (s & 1) ? I.bK[1] : I.bK[0];
+    float4* Rn = (s & 1) ? I.bR[1] : I.bR[0];
+    int4 Ka = make_int4(0, 0, 0, 0);
+    float4 Ra = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (SPLIT) {
+        Ka = Kc[a];
+        Ra = Rc[a];
+    }
     const int fa = I.bfil[a], pa = I.bpos[a];
     const int nn = I.nnbr[a];
     // loads that do not depend on the pair loop go first, so that their latency overlaps it:
@@ -522,7 +586,11 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     long long idl[CPL];
     T wdl[CPL], uc[CPL][3], gcc[CPL][3];
     unsigned flagged[CPL];
-    const StencilCell<T> sc = stencil_cell<T>(I, P);  // once per lane, whatever its corners
+    StencilCell<T> sc;  // once per lane, whatever its corners
+    if constexpr (SPLIT)
+        sc = stencil_cell_split(I, Ka, Ra);
+    else
+        sc = stencil_cell<T>(I, P);
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         const int c = lane + k * L;
@@ -560,19 +628,23 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
             same = I.bfil[b] == fa;
             sep = same ? abs(I.bpos[b] - pa) : 0;
         }
-        T d0, d1;
-        if constexpr (sizeof(T) == 8) {
+        T d0, d1, d2;
+        if constexpr (!SPLIT) {
             d0 = (T)min_image(cur[3 * b] - P[0], I.nx);
             d1 = (T)min_image(cur[3 * b + 1] - P[1], I.ny);
+            d2 = (T)(cur[3 * b + 2] - P[2]);
         } else {
-            // the FP64 difference rounded once, the periodic image taken in FP32
-            d0 = (T)(cur[3 * b] - P[0]);
-            d1 = (T)(cur[3 * b + 1] - P[1]);
-            const T hx = T(0.5) * I.nx, hy = T(0.5) * I.ny;
-            d0 = d0 > hx ? d0 - (T)I.nx : (d0 < -hx ? d0 + (T)I.nx : d0);
-            d1 = d1 > hy ? d1 - (T)I.ny : (d1 < -hy ? d1 + (T)I.ny : d1);
+            // lattice-point difference (periodic image taken on the integers) plus the
+            // difference of the offsets: one FP32 rounding, as the FP64 difference rounded
+            const int4 Kb = Kc[b];
+            const float4 Rb = Rc[b];
+            int dx = Kb.x - Ka.x, dy = Kb.y - Ka.y;
+            dx = 2 * dx > I.nx ? dx - I.nx : (2 * dx < -I.nx ? dx + I.nx : dx);
+            dy = 2 * dy > I.ny ? dy - I.ny : (2 * dy < -I.ny ? dy + I.ny : dy);
+            d0 = (T)dx + (Rb.x - Ra.x);
+            d1 = (T)dy + (Rb.y - Ra.y);
+            d2 = (T)(Kb.z - Ka.z) + (Rb.z - Ra.z);
         }
-        const T d2 = (T)(cur[3 * b + 2] - P[2]);
         const T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         const T g = pair_dUdr<T>(bp, same, sep, r, err);
         if (g != T(0)) {
@@ -602,7 +674,11 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     for (int d = 0; d < 3; ++d) drag[d] = bp.gamma * (u[d] - vt3[d]);
     T f[3] = {fx + drag[0] + bp.xi * gc[0], fy + drag[1] + bp.xi * gc[1], fz + drag[2] + bp.xi * gc[2]};
     // ---- substrate adhesion (LJ at the image distance) and load-dependent friction ----
-    const T rw = T(2) * ((T)P[2] + T(0.5));
+    T rw;  // twice the height above the substrate's image plane z = -1/2
+    if constexpr (SPLIT)
+        rw = T(2) * (((T)Ka.z + T(0.5)) + Ra.z);
+    else
+        rw = T(2) * ((T)P[2] + T(0.5));
     T fw = 0;
     if (bp.has_s && rw < bp.rc && rw > T(0)) fw = T(-2) * bp.eps_s * lj_shape_dr<T>(bp.d0, rw);
     if (bp.has_s && rw < bp.rc) {
@@ -650,6 +726,13 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
             else if (!(X > -0.5 && X < I.nz - 0.5))
                 err |= ERR_BEAD;
             nxt[3 * a + d] = X;
+            if constexpr (SPLIT) {  // the next sub-step's split form (the other buffer)
+                int K;
+                float r;
+                split_pos(X, K, r);
+                ((int*)(Kn + a))[d] = K;
+                ((float*)(Rn + a))[d] = r;
+            }
         } else {
             I.bv[3 * a + d] = v;
             if (cur != I.bx) I.bx[3 * a + d] = Pd;

@@ -150,6 +150,11 @@ constexpr int MBAR_POLLS = 1 << 16;
 // colour gradient.
 template <typename T>
 __device__ __forceinline__ T colour_q(T a, T b) { return (a - b) / (a + b); }
+// (1 + C)/2 = rho_R/(rho_R + rho_B): exactly 0 where there is no red
+template <typename T>
+__device__ __forceinline__ T liquid_fraction(T a, T b) { return a / (a + b); }
+template <>
+__device__ __forceinline__ float liquid_fraction<float>(float a, float b) { return __fdividef(a, a + b); }
 template <>
 __device__ __forceinline__ float colour_q<float>(float a, float b) {
     const float t = __fdividef(2.0f * fminf(a, b), a + b);
@@ -170,7 +175,7 @@ __device__ __forceinline__ constexpr float min_normal<float>() { return 1.175494
 template <>
 __device__ __forceinline__ constexpr double min_normal<double>() { return 2.2250738585072014e-308; }
 
-// Liquid column height h(x,y) = sum_z (1 + C)/2 of the current moments (Eq. (8))
+// Liquid column height h(x,y) = sum_z (1 + C)/2 = sum_z rho_R/rho of the current moments (Eq. (8))
 // for instances whose sink is on in this step.  A block takes 32 columns with 8
 // threads per column, each summing every 8th plane; the 8 partial sums are then
 // added in a fixed order.
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(HCOL_X * HCOL_Z) k_column_height(const InstDev
     if (c < (int)nxy)
         for (int z = threadIdx.y; z < I.nz; z += HCOL_Z) {
             const T a = rho[(unsigned)z * nxy + c], b = rho[N + (unsigned)z * nxy + c];
-            h += (T(1) + colour_q<T>(a, b)) / T(2);
+            h += liquid_fraction<T>(a, b);
         }
     part[threadIdx.y][threadIdx.x] = h;
     __syncthreads();

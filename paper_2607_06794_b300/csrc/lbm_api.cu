@@ -255,6 +255,10 @@ void carve(const lbm_config* cfgs, int n, Carver& cv, Layout& L) {
             I.bvh = (double*)cv.take(vb);
             I.bx2 = (double*)cv.take(vb);
             I.bx0 = (double*)cv.take(vb);
+            for (int b = 0; b < 2; ++b) {
+                I.bK[b] = (int4*)cv.take(sizeof(int4) * (size_t)c.max_beads);
+                I.bR[b] = (float4*)cv.take(sizeof(float4) * (size_t)c.max_beads);
+            }
             I.bfil = (int*)cv.take(sizeof(int) * c.max_beads);
             I.bpos = (int*)cv.take(sizeof(int) * c.max_beads);
             I.nbr = (int*)cv.take(sizeof(int) * (size_t)c.max_beads * MAX_NBR);

@@ -356,6 +356,12 @@ struct InstDev {
     double* bvh;
     double* bx2;
     double* bx0;
+    // sub-step positions split into the nearest lattice point and an FP32 offset
+    // (x = K + r, |r| <= 1/2), [0] mirroring bx2, [1] mirroring bx: the FP32 force
+    // path forms pair separations and the trilinear stencil from them with no FP64
+    // arithmetic (the FP64 path reads the positions themselves)
+    int4* bK[2];
+    float4* bR[2];
     int* bfil;
     int* bpos;
     int* nbr;
