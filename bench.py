@@ -33,6 +33,10 @@ METRIC = "2-comp D3Q19 MLUPS & % HBM roofline; FP16-store+batched vs FP32 plain"
 # in FP64).
 ALG_BYTES = {"fp64": 640, "fp32": 320, "fp16": 168, "bf16": 168}
 
+# B300's nominal HBM3e bandwidth (GB/s), beside the measured copy bandwidth the
+# roofline fraction is taken against
+NOMINAL_HBM_GBS = 7700.0
+
 # DRAM bytes (read + write) per launch of the fused kernel from one ncu capture of
 # the committed profiles, keyed by the hash of the kernel source when they were
 # taken, the workload and the tiling; null once any of them differs.  The DRAM
@@ -470,6 +474,7 @@ def main():
     tr = TRAFFIC.get((kh, wl.name, None if tuned is None else tuned[0]))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": tr, "peak_kind": peak_kind,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "kernel": "k_stream_collide", "ms_per_launch": round(ms_fluid, 5),
                 "alg_bytes_per_node": ALG_BYTES[prec], "kernel_src": kh,
                 "ms_per_step_direct_launch": round(ms_prof_step, 5)}
@@ -562,6 +567,10 @@ def main():
         # the smaller 256x128x64 stripe droplet with 200 wires, FP32
         w2 = workloads.droplet_c2("fp32")
         variants["c2_fp32"] = measure(w2, wire_placement(w2), args.steps)
+        # the paper's own pure-droplet domain (256x104x36 with a 116x42 patch, no wires)
+        for vp in ("fp32", "fp16"):
+            wp = workloads.paper_droplet(vp)
+            variants["paper_droplet_" + vp] = measure(wp, wire_placement(wp), args.steps)
 
     if not args.no_variants and default_run:
         # deposit analysis of Sec. II.B on the c5 wire load (16,000 beads): Kirchhoff network
