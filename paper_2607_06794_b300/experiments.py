@@ -89,7 +89,13 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
         rec = [[] for _ in range(ninst)]
         done = 0
         every_ = steps if not every else every
+        status = 0
         while True:
+            status = sim.status()
+            if status != 0:
+                # a latched failure (say a bead pushed out of the fluid): the run stops here
+                # and reports it, with the records up to the last good one
+                break
             if done % every_ == 0 or done == steps:
                 for k in range(ninst):
                     rec[k].append(dict(step=done, **sim.shape(k)))
@@ -100,9 +106,10 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
             done += n
         sim.sync()
         placed = wires or wl.wires
-        desc = [sim.descriptors(k) if placed[k] is not None else None for k in range(ninst)]
+        desc = [sim.descriptors(k) if placed[k] is not None and status == 0 else None for k in range(ninst)]
         # instance 0 at the top level; every instance under "instances"
-        out[prec] = {"series": rec[0], "final": rec[0][-1], "descriptors": desc[0], "status": sim.status(),
+        out[prec] = {"series": rec[0], "final": rec[0][-1], "descriptors": desc[0], "status": status,
+                     "stopped_at": done if status != 0 else None,
                      "instances": [{"series": rec[k], "final": rec[k][-1], "descriptors": desc[k]}
                                    for k in range(ninst)]}
         sim.close()
@@ -131,7 +138,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.compare:
         def show(prec, r):
-            print(json.dumps({"precision": prec, "status": r["status"], "descriptors": r["descriptors"],
+            print(json.dumps({"precision": prec, "status": r["status"], "stopped_at": r["stopped_at"],
+                              "descriptors": r["descriptors"],
                               "series": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
                                          for e in r["series"]]}), flush=True)
         storage_comparison(workloads.WORKLOADS[a.compare], tuple(a.precs.split(",")), a.steps, a.every,

@@ -79,6 +79,32 @@ def test_one_step_matches_oracle(lbm, oracle, prec):
     assert pop_err(got, fR, fB) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_red_free_gas_warps_match_oracle(lbm, oracle, prec):
+    """A tall gas region above a low droplet: in 16-bit storage most 32-node rows there hold
+    no red at all (the liquid fraction -1/2 exactly), and the fused kernel takes its red-free
+    form for those warps. One step against the oracle, and the rows stay red-free."""
+    cfg = droplet_cfg(lbm, nx=64, ny=24, nz=40, prec=prec, c=10.0, J0=1e-3, evap_start=0)
+    p, fR, fB, cot = oracle_state(oracle, cfg, 15)
+    sim = lbm.Simulation([cfg])
+    sim.write(0, "populations", np.stack([fR, fB]))
+    before = sim.read(0, "populations")
+    red_rows = before[0].reshape(19, cfg.nz, cfg.ny, cfg.nx // 32, 32)
+    free = np.all(red_rows == 0.0, axis=(0, 4))  # [z][y][row piece]
+    assert free.mean() > 0.4  # the red-free form is exercised
+    acc = oracle.Acc()
+    oracle.step(p, fR, fB, cot, acc)
+    sim.step(1)
+    sim.sync()
+    got = sim.read(0, "populations")
+    assert pop_err(got, fR, fB) < TOL[prec]
+    after = got[0].reshape(19, cfg.nz, cfg.ny, cfg.nx // 32, 32)
+    # a red-free row far from the liquid stays red-free (no red streams in from above)
+    top = free.copy()
+    top[: cfg.nz - 4] = False
+    assert np.all(after[:, top] == 0.0)
+
+
 def test_fp64_ten_steps_with_evaporation_and_budgets(lbm, oracle):
     cfg = droplet_cfg(lbm, prec="fp64", J0=2e-3, evap_start=0)
     sim, p, fR, fB, cot, acc, _ = run_pair(lbm, oracle, cfg, steps=10)
