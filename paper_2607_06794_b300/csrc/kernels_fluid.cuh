@@ -244,7 +244,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     // [NBUF][19 WORDS][TY][RW] words; 16-bit bulk staging is double-buffered, so the
     // copies of a plane go out a whole plane ahead
     constexpr bool ASYNC = S::WORDS > 0;
-    constexpr bool EARLY_PULL = ASYNC && !BULK && S::WORDS == 1;  // next plane's pull issued mid-plane
+    // next plane's pull issued mid-plane: 16-bit storage on 32x4 tiles (on 32x8 tiles it
+    // spilled and ran slower)
+    constexpr bool EARLY_PULL = ASYNC && !BULK && S::WORDS == 1 && TY == 4;
     static_assert(!BULK || ASYNC, "bulk staging needs word storage");
     static_assert(!(BULK && EP), "in-place storage pulls element by element");
     constexpr int RW = TX + 8;  // staged row: the tile row and 4 columns each side

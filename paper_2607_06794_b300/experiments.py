@@ -56,7 +56,9 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
     wires: per instance (centres, directions, beads per wire) placed identically in
     every run (None: the workload's own seeded placement).  Returns, per precision,
     the shape observables every `every` steps (and at the end) and the descriptors
-    and shape at the end, of instance 0 and, under "instances", of every instance."""
+    and shape at the end, of instance 0 and, under "instances", of every instance.  A run
+    whose device status latches a failure stops at the next record; its status and step
+    are reported and the state where it stopped is measured."""
     out = {}
     for prec in precs:
         wl = make(prec)
@@ -93,8 +95,12 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
         while True:
             status = sim.status()
             if status != 0:
-                # a latched failure (say a bead pushed out of the fluid): the run stops here
-                # and reports it, with the records up to the last good one
+                # a latched failure (say a bead pushed out of the fluid at the top late in the
+                # drying): the run stops here and reports it; the error is cleared so that the
+                # state where it stopped can still be measured
+                sim.clear_error()
+                for k in range(ninst):
+                    rec[k].append(dict(step=done, **sim.shape(k)))
                 break
             if done % every_ == 0 or done == steps:
                 for k in range(ninst):
@@ -106,7 +112,7 @@ def storage_comparison(make, precs=("fp64", "fp16", "bf16"), steps=1000, every=N
             done += n
         sim.sync()
         placed = wires or wl.wires
-        desc = [sim.descriptors(k) if placed[k] is not None and status == 0 else None for k in range(ninst)]
+        desc = [sim.descriptors(k) if placed[k] is not None else None for k in range(ninst)]
         # instance 0 at the top level; every instance under "instances"
         out[prec] = {"series": rec[0], "final": rec[0][-1], "descriptors": desc[0], "status": status,
                      "stopped_at": done if status != 0 else None,
