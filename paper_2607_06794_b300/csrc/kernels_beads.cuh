@@ -613,7 +613,13 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
     const double vh[3] = {I.bvh[3 * a], I.bvh[3 * a + 1], I.bvh[3 * a + 2]};
     // ---- pair forces, candidates spread over the lanes ----
     T fx = 0, fy = 0, fz = 0;
+    // candidate c >= 4 is list entry c - 4; the next candidate's index is loaded one
+    // iteration ahead, so that its latency overlaps the loads of the current pair
+    const int* nl = I.nbr + (long long)a * I.max_nbr - 4;
+    int bn = (lane >= 4 && lane < 4 + nn) ? nl[lane] : -1;
     for (int c = lane; c < 4 + nn; c += L) {
+        const int bl = bn;
+        bn = (c + L >= 4 && c + L < 4 + nn) ? nl[c + L] : -1;
         int b;
         bool same;
         int sep;
@@ -624,7 +630,7 @@ __global__ void k_bead_force(const InstDev* __restrict__ insts, StepGlobals* __r
             same = true;
             sep = k < 0 ? -k : k;
         } else {
-            b = I.nbr[(long long)a * I.max_nbr + (c - 4)];
+            b = bl;
             same = I.bfil[b] == fa;
             sep = same ? abs(I.bpos[b] - pa) : 0;
         }
