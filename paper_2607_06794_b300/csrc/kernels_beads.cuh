@@ -185,9 +185,10 @@ __global__ void k_bead_clear(const InstDev* __restrict__ insts, const StepGlobal
 
 // Step start, one warp per bead: remember the position, keep an FP32 copy
 // for the neighbour search, file the bead in its cell, take the first half
-// kick and drift of the step (FP64, lane 0), and flag the coupling tiles its
-// trilinear stencil can reach during the step (lane = one corner of the 4x4x2
-// reach; duplicates are harmless).
+// kick and drift of the step (FP64, lane 0; lanes 0..2 then split the drifted
+// position into lattice point and FP32 offset for the first sub-step), and flag
+// the coupling tiles its trilinear stencil can reach during the step (lane = one
+// corner of the 4x4x2 reach; duplicates are harmless).
 __global__ void k_bead_begin(const InstDev* __restrict__ insts, const StepGlobals* __restrict__ glob, int ahead) {
     const InstDev I = insts[blockIdx.y];
     const int lane = threadIdx.x & 31;
