@@ -101,3 +101,14 @@ def test_inplace_storage_takes_one_population_buffer(lib):
         c.inplace = 1
         one = workspace_bytes([c])
         assert abs((two - one) - (2 * 19 * 64 * 48 * 40 * eb - 2 * 10 * 64 * 48 * eb)) <= 1024
+
+
+def test_largest_lattice_is_accepted_and_one_plane_more_is_rejected(lib):
+    """Element offsets inside one population buffer are 32-bit: 2 x 19 x N must stay below
+    2^32 (N < 113,025,456 nodes); the check runs on the host, before any device call."""
+    from paper_2607_06794_b300 import Config, tiling_table
+    assert 38 * 1024 * 1024 * 107 < 2 ** 32 <= 38 * 1024 * 1024 * 108
+    tab = tiling_table([Config(1024, 1024, 107)], 0)
+    assert len(tab) > 0 and tab[:, 4].max() == 107
+    with pytest.raises(RuntimeError):
+        tiling_table([Config(1024, 1024, 108)], 0)
