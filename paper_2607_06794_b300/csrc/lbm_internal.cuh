@@ -239,11 +239,15 @@ struct Pair16 {
     }
 };
 
+// the bits of -1/2 in IEEE binary16 (sign 1, exponent 14, fraction 0)
+constexpr unsigned HALF_MINUS_HALF = 0xB800u;
+
 template <class HP, class HQ>
 struct StoreShift16 {
     using T = float;
     using E = HP;  // half-words: the deviation (HP) at even, the fraction (HQ) at odd positions
     using H = HQ;
+    static_assert(std::is_same<HQ, __half>::value, "the liquid fraction is stored in binary16");
     static constexpr int WORDS = 1;
     static __host__ __device__ __forceinline__ void decode(float P, float psi, float w, float rho0,
                                                            float& r, float& b) {
@@ -294,11 +298,12 @@ struct StoreShift16 {
         rq = r;
         bq = b;
     }
-    // an element without the red component (f^R = 0): what store gives for r = 0 (the
-    // liquid fraction -1/2, or 0 where the total is 0)
+    // an element without the red component (f^R = 0): the liquid fraction -1/2 (store
+    // writes 0 where the total is 0; the fraction only ever multiplies the total, so both
+    // decode to the same populations)
     static __device__ __forceinline__ void store_gas(E* __restrict__ p, unsigned cs, unsigned k, T w,
                                                      T rho0, T b) {
-        ((unsigned*)p)[k] = Pair16<HP, HQ>::pack(b - w * rho0, b != 0.0f ? -0.5f : 0.0f);
+        ((unsigned*)p)[k] = Cvt<HP>::bits(b - w * rho0) | (HALF_MINUS_HALF << 16);
     }
     static __device__ void to_f64(const E* p, long long cs, long long k, int i, double rho0,
                                   double& r, double& b) {
