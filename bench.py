@@ -45,14 +45,14 @@ NOMINAL_HBM_GBS = 7700.0
 # 32x4 columns; on that lattice the mixed tiling 13 is the 32-plane chunks of
 # tiling 6) scaled by the node count (8x): that capture moved 0.998 times its
 # algorithmic bytes, and a launch's traffic grows with the nodes it updates.
-_C2_TRAFFIC = 363972352 + 305786624
+_C2_TRAFFIC = 364134144 + 305696000
 _C5 = "c5_512x256x128_periodic_stripes_2000wires"
 TRAFFIC = {
-    ("2e239b5acc70", "c2_256x128x64_stripe_200wires", 13): _C2_TRAFFIC,
-    ("2e239b5acc70", "c2_256x128x64_stripe_200wires", 6): _C2_TRAFFIC,
-    ("2e239b5acc70", _C5, 13): 8 * _C2_TRAFFIC,
-    ("2e239b5acc70", _C5, 6): 8 * _C2_TRAFFIC,
-    ("2e239b5acc70", _C5, 4): 8 * _C2_TRAFFIC,
+    ("261943eb0665", "c2_256x128x64_stripe_200wires", 13): _C2_TRAFFIC,
+    ("261943eb0665", "c2_256x128x64_stripe_200wires", 6): _C2_TRAFFIC,
+    ("261943eb0665", _C5, 13): 8 * _C2_TRAFFIC,
+    ("261943eb0665", _C5, 6): 8 * _C2_TRAFFIC,
+    ("261943eb0665", _C5, 4): 8 * _C2_TRAFFIC,
 }
 
 
