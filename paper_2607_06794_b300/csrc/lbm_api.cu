@@ -367,6 +367,17 @@ constexpr size_t stage_bytes(int tx, int ty, bool bulk) {
     return (size_t)19 * S::WORDS * ty * (bulk ? tx + 8 : tx) * 4 * ((bulk && S::WORDS == 1) ? 2 : 1);
 }
 
+// Resident blocks per SM the fused kernel's register budget is sized for.  FP32 and
+// 16-bit storage: the tiling's own (128 registers a thread).  FP64: half as many blocks,
+// 255 registers a thread: the FP64 form is bound by B300's narrow FP64 pipe, not by
+// latency, and at 128 registers it spilled 1.4 KB a thread (44 bytes at 255)
+template <class S>
+struct MinBlocks {
+    static constexpr bool F64 = std::is_same<S, StoreF64>::value;
+    static constexpr int of32x8 = F64 ? 1 : 2;
+    static constexpr int of32x4 = F64 ? 2 : 4;
+};
+
 template <class S, int TX, int TY, int MINB>
 lbm_status prepare_one() {
     const size_t dyn = stage_bytes<S>(TX, TY, false);
@@ -386,8 +397,8 @@ lbm_status prepare_one() {
 // per-kernel attributes, set once before any launch or capture
 template <class S>
 lbm_status prepare_fused() {
-    lbm_status st = prepare_one<S, 32, 8, 2>();
-    if (st == LBM_OK) st = prepare_one<S, 32, 4, 4>();
+    lbm_status st = prepare_one<S, 32, 8, MinBlocks<S>::of32x8>();
+    if (st == LBM_OK) st = prepare_one<S, 32, 4, MinBlocks<S>::of32x4>();
     return st;
 }
 
@@ -401,23 +412,23 @@ lbm_status launch_fused(lbm_handle* h) {
     constexpr bool W = S::WORDS != 0;
     if (sh.tx == 32 && sh.ty == 8 && sh.minb == 2) {
         if (h->inplace)
-            k_stream_collide<S, 32, 8, 2, false, true><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(
+            k_stream_collide<S, 32, 8, MinBlocks<S>::of32x8, false, true><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(
                 in, td, h->L.glob);
         else if (bulk)
-            k_stream_collide<S, 32, 8, 2, W, false><<<nb, 256, stage_bytes<S>(32, 8, true), h->stream>>>(
+            k_stream_collide<S, 32, 8, MinBlocks<S>::of32x8, W, false><<<nb, 256, stage_bytes<S>(32, 8, true), h->stream>>>(
                 in, td, h->L.glob);
         else
-            k_stream_collide<S, 32, 8, 2, false, false><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(
+            k_stream_collide<S, 32, 8, MinBlocks<S>::of32x8, false, false><<<nb, 256, stage_bytes<S>(32, 8, false), h->stream>>>(
                 in, td, h->L.glob);
     } else if (sh.tx == 32 && sh.ty == 4 && sh.minb == 4) {
         if (h->inplace)
-            k_stream_collide<S, 32, 4, 4, false, true><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(
+            k_stream_collide<S, 32, 4, MinBlocks<S>::of32x4, false, true><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(
                 in, td, h->L.glob);
         else if (bulk)
-            k_stream_collide<S, 32, 4, 4, W, false><<<nb, 128, stage_bytes<S>(32, 4, true), h->stream>>>(
+            k_stream_collide<S, 32, 4, MinBlocks<S>::of32x4, W, false><<<nb, 128, stage_bytes<S>(32, 4, true), h->stream>>>(
                 in, td, h->L.glob);
         else
-            k_stream_collide<S, 32, 4, 4, false, false><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(
+            k_stream_collide<S, 32, 4, MinBlocks<S>::of32x4, false, false><<<nb, 128, stage_bytes<S>(32, 4, false), h->stream>>>(
                 in, td, h->L.glob);
     } else {
         return LBM_EINVAL;
