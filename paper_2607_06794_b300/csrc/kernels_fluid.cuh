@@ -65,10 +65,14 @@ __device__ T colour_ext(const InstDev& I, const T* __restrict__ rho, int x, int 
 // interior nodes are stored plainly; tile-edge and halo nodes are added
 // atomically (their buffer was zeroed one step earlier).
 // Per plane z, separated by barriers:
-//   1. issue the 38 pull loads of plane z (consumed in 3), flush plane z-2,
-//      store the prefetched C of plane z+2, prefetch C of plane z+3
-//   2. gradient and normals of plane z+1
-//   3. decode the pulled pairs, collide, recolour, evaporate, store, push
+//   1. flush plane z-2, store the prefetched C of plane z+2 (and vote whether it
+//      is pure gas, C = -1 throughout the ring), prefetch C of plane z+3; the
+//      pull of plane z is already in flight (FP64: its register loads go out here)
+//   2. gradient and normals of plane z+1, or zeros where planes z..z+2 are pure gas
+//   3. decode the pulled pairs, curvature (zero without the stencil where the normals
+//      of planes z-1..z+1 are), collide, recolour, evaporate, store, push; a warp of
+//      16-bit storage without red takes the red-free form of the collision; the pull
+//      of plane z+1 goes out after the decode (16-bit storage, 32x4 tiles) or at the end
 // ---------------------------------------------------------------------------
 // slot of a push that leaves the tile sideways, by its (c_y, c_z); |c_y| + |c_z| <= 1
 __host__ __device__ constexpr int side_slot(int dy, int dz) {
