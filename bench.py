@@ -488,6 +488,9 @@ def main():
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
+        # a run of at least 200 steps, so that the one upload of the state is amortised
+        # as in a real run, whatever K the timed region above used
+        k_e2e = max(args.steps, 200)
         c = wl.cfgs[0]
         pops = torch.empty((2, 19, c.nz, c.ny, c.nx), dtype=torch.float64, pin_memory=True)
         sim.read_into(0, "populations", pops)
@@ -499,7 +502,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.write_from(0, "populations", pops)
-        for _ in range(args.steps):
+        for _ in range(k_e2e):
             sim.step(1)
             sim.read_accum_async(0, accb)
         sim.read_into(0, "colour", colb)
@@ -509,16 +512,17 @@ def main():
         sim.write_from(0, "populations", pops)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(k_e2e):
             sim.step(1)
             sim.read_into(0, "accum", accb)
         ds = barrier_max(time.perf_counter() - t1)
-        e2e = {"value": round(world * wl.nodes * args.steps / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": int(pops.numel() * 8 // args.steps),
-               "d2h_bytes_per_step": int(48 + colb.numel() * 8 // args.steps),
-               "blocking_read_value": round(world * wl.nodes * args.steps / ds / 1e6, 2),
-               "what": "FP64 state uploaded once, K steps each with its budget record read back "
-                       "asynchronously, colour field read at the end"}
+        e2e = {"value": round(world * wl.nodes * k_e2e / dt / 1e6, 2), "unit": "MLUPS",
+               "steps": k_e2e,
+               "h2d_bytes_per_step": int(pops.numel() * 8 // k_e2e),
+               "d2h_bytes_per_step": int(48 + colb.numel() * 8 // k_e2e),
+               "blocking_read_value": round(world * wl.nodes * k_e2e / ds / 1e6, 2),
+               "what": "FP64 state uploaded once, `steps` steps (at least 200) each with its budget "
+                       "record read back asynchronously, colour field read at the end"}
         del pops, colb
     steps_lp = launches_per_step(wl)
     sim.close()
